@@ -1,0 +1,371 @@
+"""Pins of the CPU oracle against things it does not compute itself: dense
+brute force on tiny trees, exact state-vector propagation, LAPACK, SciPy's
+matrix exponential, conservation laws, convergence order and closed forms."""
+import numpy as np
+import pytest
+import scipy.linalg
+import scipy.integrate
+
+import workloads as W
+from oracle import exact, heom
+from oracle.ttn import TTN, full_state, householder_qr, expm_krylov, mode_product, qr_along
+
+
+def random_canonical(tree, rng):
+    """Random tensors in canonical gauge, centre at the root."""
+    A = []
+    for z in range(tree.n):
+        dims = tree.mode_dims(z)
+        M = rng.standard_normal((int(np.prod(dims[:-1])), dims[-1])) \
+            + 1j * rng.standard_normal((int(np.prod(dims[:-1])), dims[-1]))
+        if z > 0:
+            M, _ = np.linalg.qr(M)
+        else:
+            M = M / np.linalg.norm(M)
+        A.append(M.reshape(dims))
+    return A
+
+
+def random_sop(tree, rng, n_terms=7, max_factors=3, hermitian=False):
+    H = W.SOP(hermitian=hermitian)
+    leaves = tree.leaves()
+    for _ in range(n_terms):
+        k = rng.integers(1, max_factors + 1)
+        ls = rng.choice(leaves, size=min(k, len(leaves)), replace=False)
+        pairs = []
+        for l in ls:
+            d = int(tree.phys_dim[l])
+            pairs.append((int(l), rng.standard_normal((d, d)) + 1j * rng.standard_normal((d, d))))
+        H.add(complex(rng.standard_normal(), rng.standard_normal()), *pairs)
+    H.add(0.7)   # a constant term
+    return H
+
+
+def small_tree():
+    spec = ("node", 1, [
+        ("node", 3, [("leaf", 2, 2, "s"), ("leaf", 3, 3, "m1")]),
+        ("leaf", 3, 3, "m2"),
+        ("node", 4, [("leaf", 2, 2, "m3"), ("node", 3, [("leaf", 2, 2, "m4"), ("leaf", 3, 2, "m5")])]),
+    ])
+    return W.build_tree(spec)
+
+
+def embedding(tree, A, z):
+    """Columns: full state vectors obtained with A^z replaced by unit tensors."""
+    dims = tree.mode_dims(z)
+    S = int(np.prod(dims))
+    cols = []
+    for i in range(S):
+        B = [a.copy() for a in A]
+        e = np.zeros(S, dtype=np.complex128); e[i] = 1.0
+        B[z] = e.reshape(dims)
+        cols.append(full_state(tree, B))
+    return np.stack(cols, axis=1)
+
+
+def move_centre_to(s, target):
+    """Walk the orthogonality centre from the root down to ``target``
+    (building down-environments on the way)."""
+    path = []
+    u = target
+    while u > 0:
+        path.append(u); u = s.t.parent[u]
+    for c in reversed(path):
+        z = s.t.parent[c]
+        s._move_down(z, s.ch[z].index(c))
+
+
+# ---------------------------------------------------------------------------
+def test_heff_matches_dense_projection():
+    """Eq. psi_eom_1: H_eff at every node equals P^dag H P with P the map from
+    node coefficients to the full state (other nodes isometric)."""
+    rng = np.random.default_rng(0)
+    t = small_tree()
+    H = random_sop(t, rng)
+    Hd = exact.full_hamiltonian(t, H, dense=True)
+    for target in range(t.n):
+        s = TTN(t, H, random_canonical(t, rng))
+        move_centre_to(s, target)
+        P = embedding(t, s.A, target)
+        assert np.allclose(P.conj().T @ P, np.eye(P.shape[1]), atol=1e-12)
+        dense = P.conj().T @ Hd @ P
+        dims = t.mode_dims(target)
+        S = int(np.prod(dims))
+        mine = np.zeros((S, S), dtype=np.complex128)
+        for i in range(S):
+            e = np.zeros(S, dtype=np.complex128); e[i] = 1.0
+            mine[:, i] = s.heff(target, e.reshape(dims)).ravel()
+        assert np.abs(mine - dense).max() <= 1e-12 * max(1.0, np.abs(dense).max())
+
+
+def test_environments_from_explicit_basis_functions():
+    """Sec. II.C: h_r^z = <Phi^z|h_r|Phi^z>, H_r^z = <Psi^z|H_r|Psi^z> with the
+    SPF / SHF basis vectors written out on the full space."""
+    rng = np.random.default_rng(1)
+    t = small_tree()
+    H = random_sop(t, rng, n_terms=5)
+    leaves = t.leaves()
+    dims = [int(t.phys_dim[l]) for l in leaves]
+    for target in [3, 5, 7]:
+        s = TTN(t, H, random_canonical(t, rng))
+        move_centre_to(s, target)
+        Pz = embedding(t, s.A, target)      # columns: |Psi_i> (x) |Phi_I>
+        zd = t.mode_dims(target)
+        N = zd[-1]
+        sub = set(t.subtree_leaves(target))
+        for r in range(H.n_terms):
+            fac = {l: H.mats[m] for (l, m) in H.factors[r]}
+            def op(inside):
+                M = np.eye(1)
+                for l, d in zip(leaves, dims):
+                    X = fac[l] if (l in fac and ((l in sub) == inside)) else np.eye(d)
+                    M = np.kron(M, X)
+                return M
+            Hin, Hout = op(True), op(False)
+            # SHF block: sum over the SPF multi-index I of the projected matrix
+            Pr = Pz.reshape(-1, int(np.prod(zd[:-1])), N)
+            if s.outside[target, r]:
+                dense = np.einsum("xIi,xy,yIj->ij", Pr.conj(), Hout, Pr) / np.prod(zd[:-1])
+                assert np.allclose(s.down[target][r], dense, atol=1e-12)
+            # SPF matrix of a child of the target node (its up environment)
+            for k, c in enumerate(s.ch[target]):
+                if s.inside[c, r]:
+                    subc = set(t.subtree_leaves(c))
+                    Mc = np.eye(1)
+                    for l, d in zip(leaves, dims):
+                        X = fac[l] if (l in fac and l in subc) else np.eye(d)
+                        Mc = np.kron(Mc, X)
+                    Pk = np.moveaxis(Pz.reshape((-1,) + tuple(zd)), k + 1, -1)
+                    Pk = Pk.reshape(Pk.shape[0], -1, zd[k])
+                    dense = np.einsum("xOi,xy,yOj->ij", Pk.conj(), Mc, Pk) / (np.prod(zd) // zd[k])
+                    assert np.allclose(s.up[c][r], dense, atol=1e-12)
+
+
+def test_householder_qr_matches_lapack_up_to_phases():
+    rng = np.random.default_rng(2)
+    for (m, n) in [(7, 3), (16, 16), (40, 5), (6144 // 64, 16)]:
+        M = rng.standard_normal((m, n)) + 1j * rng.standard_normal((m, n))
+        Q, R = householder_qr(M)
+        assert np.allclose(Q @ R, M, atol=1e-13 * np.abs(M).max() * m)
+        assert np.allclose(Q.conj().T @ Q, np.eye(n), atol=1e-13)
+        assert np.all(np.abs(np.tril(R, -1)) == 0)
+        assert np.all(np.diag(R).real >= 0) and np.allclose(np.diag(R).imag, 0)
+        Ql, Rl = np.linalg.qr(M)
+        ph = np.diag(Rl) / np.abs(np.diag(Rl))
+        assert np.allclose(Q, Ql * ph[None, :], atol=1e-12)
+        assert np.allclose(R, Rl * ph.conj()[:, None], atol=1e-12 * np.abs(M).max())
+
+
+def test_householder_qr_rank_deficient():
+    """Zero columns get the identity reflector: Q stays orthonormal, M = QR,
+    and the product-state matricisation gives the leading unit vectors."""
+    rng = np.random.default_rng(3)
+    M = np.zeros((12, 4), dtype=np.complex128)
+    M[0, 0] = 1.0
+    Q, R = householder_qr(M)
+    assert np.array_equal(Q, np.eye(12, 4))
+    B = rng.standard_normal((12, 2)) + 1j * rng.standard_normal((12, 2))
+    M = np.concatenate([B, B @ np.array([[1.0, 2.0], [0.5, -1.0]])], axis=1)
+    Q, R = householder_qr(M)
+    assert np.allclose(Q.conj().T @ Q, np.eye(4), atol=1e-13)
+    assert np.allclose(Q @ R, M, atol=1e-12)
+
+
+def test_mode_product_definition():
+    rng = np.random.default_rng(4)
+    A = rng.standard_normal((3, 4, 5)) + 1j * rng.standard_normal((3, 4, 5))
+    M = rng.standard_normal((4, 4))
+    ref = np.zeros_like(A)
+    for a in range(3):
+        for p in range(4):
+            for b in range(5):
+                ref[a, p, b] = sum(M[p, m] * A[a, m, b] for m in range(4))
+    assert np.allclose(mode_product(M, A, 1), ref)
+    Q, R = qr_along(A, 1)
+    assert np.allclose(mode_product(R.T, Q, 1), A)
+
+
+@pytest.mark.parametrize("hermitian", [True, False])
+def test_krylov_exponential_matches_expm(hermitian):
+    rng = np.random.default_rng(5 + hermitian)
+    n = 60
+    X = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    Hm = (X + X.conj().T) / 2 if hermitian else X / 3
+    v = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    for tau in [0.01, 0.3, 2.0]:
+        w = expm_krylov(lambda x: Hm @ x, v, tau, hermitian)
+        ref = scipy.linalg.expm(-1j * tau * Hm) @ v
+        assert np.abs(w - ref).max() <= 1e-11 * np.linalg.norm(v) * max(1, np.abs(ref).max())
+        if hermitian:
+            assert abs(np.linalg.norm(w) - np.linalg.norm(v)) < 1e-12 * np.linalg.norm(v)
+
+
+def test_full_bond_dimension_is_exact():
+    """With bond dimensions equal to min(subtree, complement) the TTN manifold
+    is the whole space and the splitting step reproduces exact propagation."""
+    p = W.config_c1(full_bonds=True, d=4)
+    s = TTN(p.tree, p.H, p.tensors)
+    psi0 = full_state(p.tree, s.A)
+    Hd = exact.full_hamiltonian(p.tree, p.H, dense=True)
+    n = 40
+    ref = exact.propagate_eigh(Hd, psi0, [p.dt * (i + 1) for i in range(n)])
+    worst = 0.0
+    for i in range(n):
+        s.step(p.dt)
+        po = s.populations(p.obs_leaves)
+        pr = exact.leaf_populations(p.tree, ref[i], p.obs_leaves)
+        worst = max(worst, max(np.abs(a - b).max() for a, b in zip(po, pr)))
+    assert worst <= 1e-12
+
+
+def test_norm_and_energy_conserved_truncated():
+    p = W.config_c1()
+    s = TTN(p.tree, p.H, p.tensors)
+    n0, e0 = s.norm2(), s.energy()
+    s.step(p.dt, 60)
+    assert abs(s.norm2() - n0) <= 1e-11
+    assert abs(s.energy() - e0) <= 1e-11
+
+
+def test_second_order_convergence():
+    p = W.config_c1(d=6)
+    def run(dt, T=4.0):
+        s = TTN(p.tree, p.H, p.tensors)
+        s.step(dt, int(round(T / dt)))
+        return full_state(p.tree, s.A)
+    ref = run(0.4 / 32)
+    e = [np.linalg.norm(run(dt) - ref) for dt in (0.4, 0.2, 0.1)]
+    for a, b in zip(e, e[1:]):
+        assert 3.5 < a / b < 4.6
+
+
+def test_uncoupled_spin_closed_form():
+    eps, delta = 0.3, 1.0
+    p = W.config_c1(g_scale=0.0, eps=eps, delta=delta)
+    s = TTN(p.tree, p.H, p.tensors)
+    Om = np.hypot(eps, delta)
+    spin = p.meta["spin"]
+    for i in range(1, 41):
+        s.step(p.dt)
+        pop = s.populations([spin])[0]
+        t = i * p.dt
+        assert abs((pop[0] - pop[1]) - (eps ** 2 + delta ** 2 * np.cos(Om * t)) / Om ** 2) < 1e-11
+
+
+def test_free_oscillator_closed_form():
+    """Uncoupled modes in a superposition: <a>(t) = <a>(0) exp(-i w t)."""
+    p = W.config_c1(g_scale=0.0)
+    t = p.tree
+    rng = np.random.default_rng(7)
+    vecs = {}
+    for l in p.meta["modes"]:
+        v = rng.standard_normal(8) + 1j * rng.standard_normal(8)
+        vecs[l] = v / np.linalg.norm(v)
+    A = W.product_state(t, vecs)
+    s = TTN(t, p.H, A)
+    a = W.boson_ops(8)["a"]
+    a0 = {l: np.vdot(vecs[l], a @ vecs[l]) for l in vecs}
+    for i in range(1, 21):
+        s.step(p.dt)
+        G = s.shf_gram()
+        for k, l in enumerate(p.meta["modes"]):
+            rho = s.reduced_density(l, G)
+            val = np.trace(rho @ a) / np.trace(rho)     # Tr(rho a)
+            assert abs(val - a0[l] * np.exp(-1j * p.meta["w"][k] * i * p.dt)) < 1e-11
+
+
+def test_independent_boson_decoherence():
+    """Delta = 0 from |+x> (x) vacuum: <sx>(t) = prod_k exp(-4 (g_k/w_k)^2 (1 - cos w_k t))
+    (untruncated Fock space; here compared within the truncation error), and
+    exactly against same-basis diagonalisation at full bond dimension."""
+    d = 12
+    p = W.config_c1(full_bonds=True, d=d, delta=0.0, g_scale=0.3)
+    t = p.tree
+    spin = p.meta["spin"]
+    v = np.array([1.0, 1.0], dtype=np.complex128) / np.sqrt(2)
+    A = W.product_state(t, {spin: v})
+    s = TTN(t, p.H, A)
+    w, g = p.meta["w"], p.meta["g"]
+    sx = W.pauli()["x"]
+    for i in range(1, 11):
+        s.step(p.dt)
+        tt = i * p.dt
+        rho = s.reduced_density(spin)
+        val = np.real(np.trace(rho @ sx) / np.trace(rho))
+        cf = np.prod(np.exp(-4 * (g / w) ** 2 * (1 - np.cos(w * tt))))
+        assert abs(val - cf) < 1e-9
+
+
+def test_reduced_density_gauge_walk_matches_full_state():
+    rng = np.random.default_rng(8)
+    t = small_tree()
+    H = random_sop(t, rng)
+    s = TTN(t, H, random_canonical(t, rng))
+    psi = full_state(t, s.A)
+    leaves = t.leaves()
+    dims = [int(t.phys_dim[l]) for l in leaves]
+    G = s.shf_gram()
+    for l in leaves:
+        ref = exact.leaf_reduced_density(psi, dims, leaves.index(l))
+        assert np.allclose(s.reduced_density(l, G), ref, atol=1e-13)
+
+
+def test_vacuum_projection_matches_full_state():
+    rng = np.random.default_rng(9)
+    t = small_tree()
+    H = random_sop(t, rng)
+    s = TTN(t, H, random_canonical(t, rng))
+    psi = full_state(t, s.A)
+    leaves = t.leaves()
+    dims = [int(t.phys_dim[l]) for l in leaves]
+    for keep in leaves:
+        T = psi.reshape(dims)
+        idx = tuple(slice(None) if l == keep else 0 for l in leaves)
+        assert np.allclose(s.vacuum_projection(keep), T[idx], atol=1e-13)
+
+
+@pytest.mark.parametrize("Km,depth", [(0, 4), (1, 3)])
+def test_heom_ttn_matches_elementwise_hierarchy(Km, depth):
+    """The operator-form generator on a full-bond TTN reproduces rho_S from the
+    hierarchy assembled element by element from SI Eq. fpheom_SM_rescaled."""
+    p = W.config_c4(K_matsubara=Km, depth=depth, chi=1000, dt=0.02)
+    s = TTN(p.tree, p.H, p.tensors)
+    n = 30
+    ts = [p.dt * (i + 1) for i in range(n)]
+    rho0 = np.array([[1, 0], [0, 0]], dtype=np.complex128)
+    ref = heom.rho_system(p.meta["Hs"], W.pauli()["z"], p.meta["alpha"], p.meta["nu"], depth, rho0, ts)
+    for i in range(n):
+        s.step(p.dt)
+        r = s.vacuum_projection(p.meta["sys"]).reshape(2, 2)
+        assert np.abs(r - ref[i]).max() < 1e-12
+        assert abs(np.trace(ref[i]) - 1) < 1e-12
+
+
+def test_heom_pure_dephasing_closed_form():
+    al, nu = W.drude_lorentz_exponentials(0.1, 5.0, 1.0, 1)
+    ts = np.linspace(0.1, 2.0, 5)
+    rho0 = 0.5 * np.ones((2, 2), dtype=np.complex128)
+    ref = heom.rho_system(np.zeros((2, 2)), W.pauli()["z"], al, nu, 6, rho0, ts)
+    cf = heom.pure_dephasing_coherence(al, nu, ts)
+    for i in range(len(ts)):
+        assert abs(ref[i][0, 1] / 0.5 - cf[i]) < 1e-10
+
+
+def test_orthopol_discretisation_is_a_gauss_rule():
+    """Sec. II.E.1: the n-point rule integrates w^k J(w) exactly for k <= 2n-1."""
+    J = W.ohmic_J(0.5, 5.0)
+    n = 6
+    w, g = W.discretise_orthopol(J, 0.0, 50.0, n)
+    for k in range(2 * n):
+        ref = scipy.integrate.quad(lambda x: x ** k * J(x), 0.0, 50.0, limit=200)[0]
+        got = np.sum(np.pi * g ** 2 * w ** k)
+        assert abs(got - ref) <= 1e-9 * abs(ref)
+
+
+def test_product_state_is_canonical():
+    for p in [W.config_c1(), W.config_c2(), W.config_c4()]:
+        for z in range(1, p.tree.n):
+            A = p.tensors[z]
+            M = A.reshape(-1, A.shape[-1])
+            assert np.array_equal(M.conj().T @ M, np.eye(M.shape[1]))
+        assert np.linalg.norm(p.tensors[0]) == 1.0
