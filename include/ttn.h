@@ -1,0 +1,194 @@
+/*
+ * libttn -- tree tensor network (ML-MCTDH) time evolution on one GB300 GPU.
+ *
+ * C ABI.  Plain pointers and sizes only; no exceptions cross it.
+ *
+ * The state is a tree tensor network (paper Sec. II.A, Eqs.
+ * wavefunction_expansion_spf, spf_recursion): one coefficient tensor per node,
+ * stored row-major with shape [n_1, ..., n_d, N] -- the bond dimensions of the
+ * node's children in child order (a leaf has a single physical index of
+ * dimension d instead), then the bond to its parent N (the root's N is 1).
+ * Complex numbers are interleaved (re, im) doubles.
+ *
+ * The Hamiltonian is a sum of products (Sec. II.B.1, Eq. sop_ham),
+ *     H = sum_r c_r  prod_{f in term r}  M_f  (acting on leaf(f)),
+ * with hbar = 1.  Time stepping is the one-site projector-splitting
+ * integrator (Sec. II.C, Eq. psi_eom_1): every node tensor is propagated
+ * under its effective Hamiltonian, bonds are propagated backwards between
+ * node updates, QR factorisations move the orthogonality centre.  One step
+ * of length dt is the symmetric composition of a forward and a reverse
+ * sweep of length dt/2 each.
+ *
+ * Ownership: the caller owns every array passed in; the library copies what
+ * it keeps before returning, so inputs may be freed on return.  Outputs go
+ * to caller-allocated host buffers.  A context owns its device memory
+ * (allocated with cudaMalloc on the current device at ttn_create, released
+ * by ttn_destroy) and runs its work on the stream given by ttn_set_stream
+ * (default: the legacy default stream).
+ *
+ * Errors: every call returns a ttn_status.  TTN_E_INVALID leaves the context
+ * unchanged; a CUDA or device-side failure (TTN_E_CUDA, TTN_E_NOCONV,
+ * TTN_E_TIMEOUT) marks the context as failed, after which only ttn_get_state,
+ * ttn_last_error and ttn_destroy are meaningful (TTN_E_STATE otherwise).
+ * ttn_last_error returns a message describing the most recent failure.
+ */
+#ifndef TTN_H
+#define TTN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ttn_ctx ttn_ctx;
+typedef struct { double re, im; } ttn_c128;
+
+typedef enum {
+    TTN_OK = 0,
+    TTN_E_INVALID = 1,   /* bad argument; nothing changed                          */
+    TTN_E_OOM = 2,       /* device or host allocation failed                       */
+    TTN_E_CUDA = 3,      /* a CUDA runtime call failed                              */
+    TTN_E_NOCONV = 4,    /* Krylov exponential did not converge after substepping   */
+    TTN_E_TIMEOUT = 5,   /* a bounded device-side wait gave up                      */
+    TTN_E_STATE = 6      /* call not valid in the context's current state           */
+} ttn_status;
+
+/* Arithmetic of the bulk contractions.  TTN_FP64: everything in complex128.
+ * TTN_MIXED: effective-Hamiltonian and environment products, Krylov vectors
+ * and environment matrices in complex64 with FP32 accumulation; node
+ * tensors, the QR gauge steps, Krylov coefficients and Gram-Schmidt
+ * reductions, norms and the small projected exponential in FP64. */
+enum { TTN_FP64 = 0, TTN_MIXED = 1 };
+
+typedef struct {
+    double krylov_tol;   /* stop when Saad's a-posteriori error estimate of the
+                            projected exponential is below krylov_tol * ||v||;
+                            <= 0 selects 1e-13 (FP64) or 1e-8 (MIXED)            */
+    int krylov_maxdim;   /* Krylov dimension before the interval is halved,
+                            1..32; <= 0 selects 32                               */
+    double eps_spawn;    /* subspace-expansion tolerance (Sec. II.D); unused
+                            while expand == 0                                    */
+    int chi_max;         /* bond-dimension cap for expansion; unused while
+                            expand == 0                                          */
+    int expand;          /* 0: fixed bond dimensions                              */
+    double qr_rank_tol;  /* a QR column whose remainder has norm <= qr_rank_tol
+                            * ||M||_F is treated as zero and completed by the
+                            deterministic unit vector (unoccupied function);
+                            <= 0 selects 1e-10 (FP64) or 1e-8 (MIXED)            */
+} ttn_step_opts;
+
+/* Create a context for a tree (Sec. II.A).
+ *   n_nodes   number of nodes, 1..65535.
+ *   parent    [n_nodes]; parent[0] = -1 (root), 0 <= parent[i] < i otherwise.
+ *             Children of a node are ordered by their index; the sweep visits
+ *             them in that order.
+ *   phys_dim  [n_nodes]; > 0 for leaves (local dimension of the single
+ *             physical mode), 0 for interior nodes.  Leaves have no children,
+ *             interior nodes at least one.
+ *   bond_dim  [n_nodes]; bond to the parent (ignored for the root).  Every
+ *             matricisation used by the sweep must have at least as many rows
+ *             as columns: a node's parent bond is at most the product of its
+ *             other index dimensions, and so is each child bond.
+ *   precision TTN_FP64 or TTN_MIXED.
+ * Allocates the context's device memory on the current CUDA device.  The
+ * state is the product state with every leaf in basis state 0 (see
+ * ttn_set_product_state); there is no Hamiltonian until
+ * ttn_set_sop_hamiltonian. */
+ttn_status ttn_create(int n_nodes, const int* parent, const int* phys_dim,
+                      const int* bond_dim, int precision, ttn_ctx** out);
+
+/* Set every node tensor.  tensors holds the tensors back to back, node z at
+ * tensors[offsets[z] .. offsets[z+1]) (offsets has n_nodes+1 entries; sizes
+ * must match the node shapes).  The caller promises canonical gauge with
+ * the orthogonality centre at the root: each non-root tensor, matricised as
+ * [prod(child dims) x N], has orthonormal columns.  Environments are
+ * rebuilt if a Hamiltonian is set. */
+ttn_status ttn_set_state(ttn_ctx* ctx, const ttn_c128* tensors, const int64_t* offsets);
+
+/* Product state prod_leaf |v_leaf> (Sec. IV.A: a product state carried with
+ * unoccupied single-particle functions).  leaf_vecs[leaf_offsets[z] ..
+ * +phys_dim[z]) is the (not necessarily normalised, nonzero) vector of leaf
+ * z; leaf_offsets has n_nodes entries, entries of interior nodes are
+ * ignored.  Unoccupied functions are fixed deterministically: a leaf's
+ * column 0 is v/|v|, further columns are the lowest-index unit vectors made
+ * orthogonal to the previous ones (two Gram-Schmidt passes; a remainder of
+ * norm < 1/2 is skipped); an interior node's column i is the unit tensor at
+ * the i-th child multi-index in row-major order; the root holds a single 1
+ * at (0, ..., 0). */
+ttn_status ttn_set_product_state(ttn_ctx* ctx, const ttn_c128* leaf_vecs,
+                                 const int64_t* leaf_offsets);
+
+/* Sum-of-product Hamiltonian (Sec. II.B.1, Eq. sop_ham).
+ *   coeff         [n_terms] c_r.
+ *   term_ptr      [n_terms+1] CSR: the factors of term r are
+ *                 term_ptr[r] .. term_ptr[r+1]-1 (a term with no factors is
+ *                 the constant c_r).
+ *   factor_leaf   node id of each factor; must be a leaf, at most one factor
+ *                 per leaf and term.
+ *   factor_mats / factor_mat_off: the d x d row-major matrix of factor f
+ *                 starts at factor_mats[factor_mat_off[f]].
+ *   hermitian     1 if H is Hermitian (Lanczos), 0 otherwise (Arnoldi; e.g.
+ *                 the HEOM generator of Sec. II.E.3, Eq. fpheom_op).
+ * The library groups terms per node (identity factors skipped, terms acting
+ * inside one subtree pre-summed, terms that differ in one factor only
+ * combined), which is exact, and builds all environments. */
+ttn_status ttn_set_sop_hamiltonian(ttn_ctx* ctx, int n_terms, const ttn_c128* coeff,
+                                   const int* term_ptr, const int* factor_leaf,
+                                   const ttn_c128* factor_mats, const int64_t* factor_mat_off,
+                                   int hermitian);
+
+/* Advance by nsteps steps of length dt (Sec. II.C).  opts may be NULL
+ * (defaults).  Blocks until the device work has finished. */
+ttn_status ttn_step(ttn_ctx* ctx, double dt, int nsteps, const ttn_step_opts* opts);
+
+/* Advance n independent contexts (same precision) by nsteps steps of dt in
+ * one device launch, one thread block per context; the stream of ctxs[0]
+ * is used.  Contexts may have different trees and Hamiltonians. */
+ttn_status ttn_step_batch(ttn_ctx* const* ctxs, int n, double dt, int nsteps,
+                          const ttn_step_opts* opts);
+
+/* Reduced density matrix of a leaf's physical mode, normalised by <Psi|Psi>:
+ * rho[a, a'] = <Psi| (|a'><a|) |Psi> / <Psi|Psi>, written row-major to
+ * out[d*d]. */
+ttn_status ttn_reduced_density(ttn_ctx* ctx, int leaf, ttn_c128* out);
+
+/* <Psi|O|Psi>/<Psi|Psi> for n_obs single-leaf operators: O_i is the d x d
+ * row-major matrix at ops[op_off[i]] acting on leaf[i]. */
+ttn_status ttn_expect(ttn_ctx* ctx, int n_obs, const int* leaf, const ttn_c128* ops,
+                      const int64_t* op_off, ttn_c128* out);
+
+/* <Psi|Psi> and <Psi|H|Psi>/<Psi|Psi>. */
+ttn_status ttn_norm_energy(ttn_ctx* ctx, double* norm2, ttn_c128* energy);
+
+/* Contract every leaf except keep_leaf with its basis vector 0 and write the
+ * remaining vector over keep_leaf's physical index to out[d] (for the HEOM
+ * generator this is rho_S = <0_bath|rho), paper SI Sec. S2). */
+ttn_status ttn_vacuum_projection(ttn_ctx* ctx, int keep_leaf, ttn_c128* out);
+
+/* Copy all node tensors to the host, in the layout of ttn_set_state;
+ * offsets (n_nodes+1 entries) receives the layout. */
+ttn_status ttn_get_state(ttn_ctx* ctx, ttn_c128* tensors, int64_t* offsets);
+
+/* Bond dimension of every node to its parent (root: 1), out[n_nodes]. */
+ttn_status ttn_bond_dims(ttn_ctx* ctx, int* out);
+
+/* Run all further work of the context on this cudaStream_t. */
+ttn_status ttn_set_stream(ttn_ctx* ctx, void* cuda_stream);
+
+/* Device memory held by the context, in bytes. */
+ttn_status ttn_device_bytes(const ttn_ctx* ctx, size_t* bytes);
+
+/* Message for the most recent failure of a call on ctx (or of ttn_create
+ * when ctx is NULL).  Valid until the next call on the same context. */
+const char* ttn_last_error(const ttn_ctx* ctx);
+
+/* Release the context and its device memory.  NULL is ignored. */
+void ttn_destroy(ttn_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TTN_H */

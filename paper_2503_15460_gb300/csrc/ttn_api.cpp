@@ -1,0 +1,493 @@
+// libttn C ABI (declarations and documentation in include/ttn.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/ttn.h"
+#include "ttn_launch.h"
+#include "ttn_plan.hpp"
+
+using ttn::cplx;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct DevProgram {
+    TtnOp* d_ops = nullptr;
+    int n_ops = 0;
+};
+
+}  // namespace
+
+struct ttn_ctx {
+    int precision = 0;
+    ttn::Tree tree;
+    ttn::Hamiltonian ham;
+    bool has_h = false;
+    ttn::Plan plan;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    std::string err;
+    bool failed = false;
+
+    char* d_state = nullptr;       // tensors, bond, workspace, status, scalars, stamps
+    size_t state_bytes = 0;
+    char* d_ops = nullptr;         // slot storage, slot table, entries, op lists, instances
+    size_t ops_bytes = 0;
+    TtnSlot* d_slots = nullptr;
+    TtnEntry* d_entries = nullptr;
+    DevProgram init_p, step_p, ne_p;
+    std::vector<DevProgram> rdm_p, vac_p;
+    TtnInstance* d_inst = nullptr; // staging for single-instance launches
+    TtnInstance* d_batch = nullptr;
+    int batch_cap = 0;
+    double ktol = 0.0;
+    double qtol = 0.0;
+    int kmax = TTN_KMAX;
+};
+
+namespace {
+
+ttn_status fail(ttn_ctx* c, ttn_status s, const std::string& msg) {
+    if (c) {
+        c->err = msg;
+        if (s == TTN_E_CUDA || s == TTN_E_NOCONV || s == TTN_E_TIMEOUT) c->failed = true;
+    } else {
+        g_create_error = msg;
+    }
+    return s;
+}
+
+ttn_status cuda_fail(ttn_ctx* c, cudaError_t e, const char* what) {
+    return fail(c, TTN_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                  \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+    } while (0)
+
+// Convert host complex128 data into the bulk element type.
+std::vector<char> to_bulk(const cplx* src, size_t n, size_t esz) {
+    std::vector<char> out(n * esz);
+    if (esz == 16) {
+        std::memcpy(out.data(), src, n * 16);
+    } else {
+        float* f = (float*)out.data();
+        for (size_t i = 0; i < n; ++i) { f[2 * i] = (float)src[i].real(); f[2 * i + 1] = (float)src[i].imag(); }
+    }
+    return out;
+}
+
+void from_bulk(const char* src, size_t n, size_t esz, cplx* dst) {
+    if (esz == 16) { std::memcpy(dst, src, n * 16); return; }
+    const float* f = (const float*)src;
+    for (size_t i = 0; i < n; ++i) dst[i] = cplx(f[2 * i], f[2 * i + 1]);
+}
+
+TtnInstance make_instance(ttn_ctx* c, const DevProgram& p) {
+    TtnInstance in{};
+    in.ops = p.d_ops;
+    in.n_ops = p.n_ops;
+    in.n_slots = (int)c->plan.slots.size();
+    in.entries = c->d_entries;
+    in.slots = c->d_slots;
+    in.work = c->d_state + c->plan.work_off;
+    in.smax = c->plan.smax;
+    in.status = (int*)(c->d_state + c->plan.status_off);
+    in.steps_done = (int*)(c->d_state + c->plan.steps_off);
+    in.stamps = (unsigned long long*)(c->d_state + c->plan.stamps_off);
+    in.ktol = c->ktol > 0 ? c->ktol : (c->precision == TTN_MIXED ? 1e-8 : 1e-13);
+    in.qtol = c->qtol > 0 ? c->qtol : (c->precision == TTN_MIXED ? 1e-8 : 1e-10);
+    in.kmax = c->kmax;
+    return in;
+}
+
+ttn_status check_status(ttn_ctx* c) {
+    int st = 0;
+    CK(cudaMemcpyAsync(&st, c->d_state + c->plan.status_off, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "status copy");
+    CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+    if (st == 4) return fail(c, TTN_E_NOCONV, "Krylov exponential did not converge");
+    if (st == 5) return fail(c, TTN_E_TIMEOUT, "device wait timed out");
+    if (st != 0) return fail(c, TTN_E_CUDA, "device reported status " + std::to_string(st));
+    return TTN_OK;
+}
+
+ttn_status run_program(ttn_ctx* c, const DevProgram& p, double dt, int nrep) {
+    if (p.n_ops == 0 || nrep == 0) return TTN_OK;
+    TtnInstance in = make_instance(c, p);
+    CK(cudaMemcpyAsync(c->d_inst, &in, sizeof(in), cudaMemcpyHostToDevice, c->stream), "instance upload");
+    int e = ttn_launch_program(c->precision, c->d_inst, 1, dt, nrep, c->stream);
+    if (e != 0) return cuda_fail(c, (cudaError_t)e, "kernel launch");
+    return check_status(c);
+}
+
+void free_ops(ttn_ctx* c) {
+    if (c->d_ops) cudaFree(c->d_ops);
+    c->d_ops = nullptr;
+    c->ops_bytes = 0;
+    c->d_slots = nullptr;
+    c->d_entries = nullptr;
+    c->init_p = c->step_p = c->ne_p = DevProgram();
+    c->rdm_p.clear(); c->vac_p.clear();
+    c->d_inst = nullptr;
+}
+
+// Allocate and fill the operator arena for the current plan.
+ttn_status upload_ops(ttn_ctx* c) {
+    ttn::Plan& P = c->plan;
+    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+    size_t slot_bytes = 0;
+    for (auto& s : P.slots) slot_bytes = std::max(slot_bytes, (size_t)s.off + (size_t)s.rows * s.cols * P.esz);
+    slot_bytes = al(slot_bytes);
+    std::vector<const ttn::Program*> progs{&P.init_prog, &P.step_prog, &P.norm_energy_prog};
+    for (auto& p : P.rdm_prog) progs.push_back(&p);
+    for (auto& p : P.vac_prog) progs.push_back(&p);
+    size_t n_ops_total = 0;
+    for (auto* p : progs) n_ops_total += p->ops.size();
+    size_t off_table = slot_bytes;
+    size_t off_entries = al(off_table + P.slots.size() * sizeof(TtnSlot));
+    size_t off_ops = al(off_entries + std::max<size_t>(1, P.entries.size()) * sizeof(TtnEntry));
+    size_t off_inst = al(off_ops + std::max<size_t>(1, n_ops_total) * sizeof(TtnOp));
+    size_t total = al(off_inst + sizeof(TtnInstance));
+    free_ops(c);
+    CK(cudaMalloc(&c->d_ops, total), "cudaMalloc (operators)");
+    c->ops_bytes = total;
+    std::vector<char> host(total, 0);
+    // constant slots
+    for (auto& s : P.slots)
+        if (s.constant) {
+            auto b = to_bulk(s.data.data(), s.data.size(), P.esz);
+            std::memcpy(host.data() + s.off, b.data(), b.size());
+        }
+    // slot table
+    std::vector<TtnSlot> table(P.slots.size());
+    for (size_t i = 0; i < P.slots.size(); ++i) {
+        table[i].ptr = c->d_ops + P.slots[i].off;
+        table[i].rows = P.slots[i].rows;
+        table[i].cols = P.slots[i].cols;
+    }
+    std::memcpy(host.data() + off_table, table.data(), table.size() * sizeof(TtnSlot));
+    std::memcpy(host.data() + off_entries, P.entries.data(), P.entries.size() * sizeof(TtnEntry));
+    // programs
+    size_t cur = off_ops;
+    auto link = [&](const ttn::Program& p) {
+        DevProgram d;
+        d.d_ops = (TtnOp*)(c->d_ops + cur);
+        d.n_ops = (int)p.ops.size();
+        for (auto& s : p.ops) {
+            TtnOp o = s.op;
+            o.a = s.a_off >= 0 ? (void*)(c->d_state + s.a_off) : nullptr;
+            o.b = s.b_off >= 0 ? (void*)(c->d_state + s.b_off) : nullptr;
+            o.out = s.out_off >= 0 ? (double*)(c->d_state + s.out_off) : nullptr;
+            std::memcpy(host.data() + cur, &o, sizeof(TtnOp));
+            cur += sizeof(TtnOp);
+        }
+        return d;
+    };
+    c->init_p = link(P.init_prog);
+    c->step_p = link(P.step_prog);
+    c->ne_p = link(P.norm_energy_prog);
+    for (auto& p : P.rdm_prog) c->rdm_p.push_back(link(p));
+    for (auto& p : P.vac_prog) c->vac_p.push_back(link(p));
+    c->d_slots = (TtnSlot*)(c->d_ops + off_table);
+    c->d_entries = (TtnEntry*)(c->d_ops + off_entries);
+    c->d_inst = (TtnInstance*)(c->d_ops + off_inst);
+    CK(cudaMemcpyAsync(c->d_ops, host.data(), total, cudaMemcpyHostToDevice, c->stream), "operator upload");
+    CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+    return TTN_OK;
+}
+
+ttn_status upload_state(ttn_ctx* c, const std::vector<std::vector<cplx>>& A) {
+    std::vector<char> host(c->plan.bond_off, 0);
+    for (int z = 0; z < c->tree.n; ++z) {
+        std::memcpy(host.data() + c->plan.tensor_off[z], A[z].data(), A[z].size() * 16);
+    }
+    CK(cudaMemcpyAsync(c->d_state, host.data(), host.size(), cudaMemcpyHostToDevice, c->stream), "state upload");
+    CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+    return TTN_OK;
+}
+
+ttn_status usable(ttn_ctx* c) {
+    if (!c) return TTN_E_INVALID;
+    if (c->failed) return fail(c, TTN_E_STATE, "context is in a failed state: " + c->err);
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    return TTN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ttn_status ttn_create(int n_nodes, const int* parent, const int* phys_dim, const int* bond_dim, int precision,
+                      ttn_ctx** out) {
+    if (!out) return fail(nullptr, TTN_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (precision != TTN_FP64 && precision != TTN_MIXED) return fail(nullptr, TTN_E_INVALID, "precision must be TTN_FP64 or TTN_MIXED");
+    ttn::Tree t;
+    std::string msg = ttn::build_tree(n_nodes, parent, phys_dim, bond_dim, t);
+    if (!msg.empty()) return fail(nullptr, TTN_E_INVALID, msg);
+    ttn_ctx* c = new (std::nothrow) ttn_ctx();
+    if (!c) return fail(nullptr, TTN_E_OOM, "host allocation failed");
+    c->precision = precision;
+    c->tree = t;
+    cudaGetDevice(&c->device);
+    ttn::make_plan(c->tree, nullptr, precision, c->plan);
+    cudaError_t e = cudaMalloc(&c->d_state, c->plan.total_bytes);
+    if (e != cudaSuccess) {
+        g_create_error = std::string("cudaMalloc (state): ") + cudaGetErrorString(e);
+        delete c;
+        return e == cudaErrorMemoryAllocation ? TTN_E_OOM : TTN_E_CUDA;
+    }
+    c->state_bytes = c->plan.total_bytes;
+    cudaMemset(c->d_state, 0, c->state_bytes);
+    ttn_status s = upload_ops(c);
+    if (s != TTN_OK) { g_create_error = c->err; ttn_destroy(c); return s; }
+    std::vector<std::vector<cplx>> vecs(t.n), A;
+    for (int z = 0; z < t.n; ++z)
+        if (t.leaf(z)) { vecs[z].assign(t.phys[z], 0.0); vecs[z][0] = 1.0; }
+    ttn::product_state(t, vecs, A);
+    s = upload_state(c, A);
+    if (s != TTN_OK) { g_create_error = c->err; ttn_destroy(c); return s; }
+    *out = c;
+    return TTN_OK;
+}
+
+ttn_status ttn_set_state(ttn_ctx* c, const ttn_c128* tensors, const int64_t* offsets) {
+    ttn_status u = usable(c); if (u) return u;
+    if (!tensors || !offsets) return fail(c, TTN_E_INVALID, "null tensors / offsets");
+    std::vector<std::vector<cplx>> A(c->tree.n);
+    for (int z = 0; z < c->tree.n; ++z) {
+        if (offsets[z + 1] - offsets[z] != c->tree.size[z])
+            return fail(c, TTN_E_INVALID, "tensor " + std::to_string(z) + " has the wrong size");
+        const cplx* p = (const cplx*)(tensors + offsets[z]);
+        A[z].assign(p, p + c->tree.size[z]);
+        for (auto& v : A[z])
+            if (!std::isfinite(v.real()) || !std::isfinite(v.imag())) return fail(c, TTN_E_INVALID, "non-finite tensor entry");
+    }
+    ttn_status s = upload_state(c, A);
+    if (s) return s;
+    if (c->has_h) return run_program(c, c->init_p, 0.0, 1);
+    return TTN_OK;
+}
+
+ttn_status ttn_set_product_state(ttn_ctx* c, const ttn_c128* leaf_vecs, const int64_t* leaf_offsets) {
+    ttn_status u = usable(c); if (u) return u;
+    if (!leaf_vecs || !leaf_offsets) return fail(c, TTN_E_INVALID, "null leaf vectors");
+    std::vector<std::vector<cplx>> vecs(c->tree.n), A;
+    for (int z = 0; z < c->tree.n; ++z) {
+        if (!c->tree.leaf(z)) continue;
+        const cplx* p = (const cplx*)(leaf_vecs + leaf_offsets[z]);
+        vecs[z].assign(p, p + c->tree.phys[z]);
+        double nrm = 0;
+        for (auto& v : vecs[z]) nrm += std::norm(v);
+        if (!(nrm > 0) || !std::isfinite(nrm)) return fail(c, TTN_E_INVALID, "leaf vector " + std::to_string(z) + " is zero or not finite");
+    }
+    ttn::product_state(c->tree, vecs, A);
+    ttn_status s = upload_state(c, A);
+    if (s) return s;
+    if (c->has_h) return run_program(c, c->init_p, 0.0, 1);
+    return TTN_OK;
+}
+
+ttn_status ttn_set_sop_hamiltonian(ttn_ctx* c, int n_terms, const ttn_c128* coeff, const int* term_ptr,
+                                   const int* factor_leaf, const ttn_c128* factor_mats,
+                                   const int64_t* factor_mat_off, int hermitian) {
+    ttn_status u = usable(c); if (u) return u;
+    if (n_terms > 0 && term_ptr && term_ptr[n_terms] > 0 && (!factor_leaf || !factor_mats || !factor_mat_off))
+        return fail(c, TTN_E_INVALID, "null factor arrays");
+    ttn::Hamiltonian h;
+    std::string msg = ttn::build_hamiltonian(c->tree, n_terms, (const cplx*)coeff, term_ptr, factor_leaf,
+                                             (const cplx*)factor_mats, factor_mat_off, hermitian, h);
+    if (!msg.empty()) return fail(c, TTN_E_INVALID, msg);
+    ttn::Plan P;
+    msg = ttn::make_plan(c->tree, &h, c->precision, P);
+    if (!msg.empty()) return fail(c, TTN_E_INVALID, msg);
+    c->ham = h;
+    c->has_h = true;
+    c->plan = P;
+    ttn_status s = upload_ops(c);
+    if (s) { c->failed = true; return s; }
+    return run_program(c, c->init_p, 0.0, 1);
+}
+
+ttn_status ttn_step(ttn_ctx* c, double dt, int nsteps, const ttn_step_opts* opts) {
+    ttn_status u = usable(c); if (u) return u;
+    if (!c->has_h) return fail(c, TTN_E_STATE, "no Hamiltonian set");
+    if (nsteps < 0 || !std::isfinite(dt)) return fail(c, TTN_E_INVALID, "bad dt / nsteps");
+    if (opts) {
+        if (opts->expand) return fail(c, TTN_E_INVALID, "subspace expansion is not enabled in this build");
+        if (opts->krylov_maxdim > TTN_KMAX) return fail(c, TTN_E_INVALID, "krylov_maxdim must be <= 32");
+        c->ktol = opts->krylov_tol;
+        c->qtol = opts->qr_rank_tol;
+        c->kmax = opts->krylov_maxdim > 0 ? opts->krylov_maxdim : TTN_KMAX;
+    }
+    return run_program(c, c->step_p, dt, nsteps);
+}
+
+ttn_status ttn_step_batch(ttn_ctx* const* ctxs, int n, double dt, int nsteps, const ttn_step_opts* opts) {
+    if (!ctxs || n <= 0) return TTN_E_INVALID;
+    ttn_ctx* c = ctxs[0];
+    for (int i = 0; i < n; ++i) {
+        ttn_status u = usable(ctxs[i]); if (u) return u;
+        if (!ctxs[i]->has_h) return fail(ctxs[i], TTN_E_STATE, "no Hamiltonian set");
+        if (ctxs[i]->precision != c->precision) return fail(c, TTN_E_INVALID, "mixed precisions in one batch");
+        if (opts) {
+            if (opts->expand) return fail(c, TTN_E_INVALID, "subspace expansion is not enabled in this build");
+            ctxs[i]->ktol = opts->krylov_tol;
+            ctxs[i]->qtol = opts->qr_rank_tol;
+            ctxs[i]->kmax = opts->krylov_maxdim > 0 ? std::min(opts->krylov_maxdim, TTN_KMAX) : TTN_KMAX;
+        }
+    }
+    if (c->batch_cap < n) {
+        if (c->d_batch) cudaFree(c->d_batch);
+        c->d_batch = nullptr;
+        CK(cudaMalloc(&c->d_batch, sizeof(TtnInstance) * n), "cudaMalloc (batch)");
+        c->batch_cap = n;
+    }
+    std::vector<TtnInstance> ins(n);
+    for (int i = 0; i < n; ++i) ins[i] = make_instance(ctxs[i], ctxs[i]->step_p);
+    CK(cudaMemcpyAsync(c->d_batch, ins.data(), sizeof(TtnInstance) * n, cudaMemcpyHostToDevice, c->stream), "batch upload");
+    int e = ttn_launch_program(c->precision, c->d_batch, n, dt, nsteps, c->stream);
+    if (e != 0) return cuda_fail(c, (cudaError_t)e, "kernel launch");
+    CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+    for (int i = 0; i < n; ++i) {
+        ctxs[i]->stream = ctxs[i]->stream;
+        ttn_status s = check_status(ctxs[i]);
+        if (s) return s;
+    }
+    return TTN_OK;
+}
+
+ttn_status ttn_norm_energy(ttn_ctx* c, double* norm2, ttn_c128* energy) {
+    ttn_status u = usable(c); if (u) return u;
+    ttn_status s = run_program(c, c->ne_p, 0.0, 1);
+    if (s) return s;
+    double sc[4] = {0, 0, 0, 0};
+    CK(cudaMemcpyAsync(sc, c->d_state + c->plan.scal_off, sizeof(sc), cudaMemcpyDeviceToHost, c->stream), "scalar copy");
+    CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+    if (norm2) *norm2 = sc[0];
+    if (energy) {
+        if (!c->has_h) return fail(c, TTN_E_STATE, "no Hamiltonian set");
+        energy->re = sc[2] / sc[0];
+        energy->im = sc[3] / sc[0];
+    }
+    return TTN_OK;
+}
+
+ttn_status ttn_reduced_density(ttn_ctx* c, int leaf, ttn_c128* out) {
+    ttn_status u = usable(c); if (u) return u;
+    if (leaf < 0 || leaf >= c->tree.n || !c->tree.leaf(leaf) || !out) return fail(c, TTN_E_INVALID, "leaf must be a leaf node");
+    ttn_status s = run_program(c, c->rdm_p[leaf], 0.0, 1);
+    if (s) return s;
+    double nrm = 0;
+    s = ttn_norm_energy(c, &nrm, nullptr);
+    if (s) return s;
+    int d = c->tree.phys[leaf];
+    const ttn::SlotInfo& sl = c->plan.slots[c->plan.rdm_slot[leaf]];
+    std::vector<char> raw(d * d * c->plan.esz);
+    CK(cudaMemcpyAsync(raw.data(), c->d_ops + sl.off, raw.size(), cudaMemcpyDeviceToHost, c->stream), "rdm copy");
+    CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+    std::vector<cplx> g(d * d);
+    from_bulk(raw.data(), d * d, c->plan.esz, g.data());
+    // the device computes conj(rho) * <Psi|Psi>
+    for (int i = 0; i < d * d; ++i) {
+        cplx v = std::conj(g[i]) / nrm;
+        out[i].re = v.real(); out[i].im = v.imag();
+    }
+    return TTN_OK;
+}
+
+ttn_status ttn_expect(ttn_ctx* c, int n_obs, const int* leaf, const ttn_c128* ops, const int64_t* op_off, ttn_c128* out) {
+    ttn_status u = usable(c); if (u) return u;
+    if (n_obs < 0 || (n_obs > 0 && (!leaf || !ops || !op_off || !out))) return fail(c, TTN_E_INVALID, "bad arguments");
+    for (int i = 0; i < n_obs; ++i) {
+        int l = leaf[i];
+        if (l < 0 || l >= c->tree.n || !c->tree.leaf(l)) return fail(c, TTN_E_INVALID, "leaf must be a leaf node");
+        int d = c->tree.phys[l];
+        std::vector<ttn_c128> rho(d * d);
+        ttn_status s = ttn_reduced_density(c, l, rho.data());
+        if (s) return s;
+        cplx acc = 0;
+        for (int a = 0; a < d; ++a)
+            for (int b = 0; b < d; ++b) {
+                cplx o(ops[op_off[i] + b * d + a].re, ops[op_off[i] + b * d + a].im);
+                acc += cplx(rho[a * d + b].re, rho[a * d + b].im) * o;
+            }
+        out[i].re = acc.real(); out[i].im = acc.imag();
+    }
+    return TTN_OK;
+}
+
+ttn_status ttn_vacuum_projection(ttn_ctx* c, int keep_leaf, ttn_c128* out) {
+    ttn_status u = usable(c); if (u) return u;
+    if (keep_leaf < 0 || keep_leaf >= c->tree.n || !c->tree.leaf(keep_leaf) || !out) return fail(c, TTN_E_INVALID, "keep_leaf must be a leaf");
+    ttn_status s = run_program(c, c->vac_p[keep_leaf], 0.0, 1);
+    if (s) return s;
+    int d = c->tree.phys[keep_leaf];
+    const ttn::SlotInfo& sl = c->plan.slots[c->plan.vac_slot[keep_leaf]];
+    std::vector<char> raw(d * c->plan.esz);
+    CK(cudaMemcpyAsync(raw.data(), c->d_ops + sl.off, raw.size(), cudaMemcpyDeviceToHost, c->stream), "vector copy");
+    CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+    from_bulk(raw.data(), d, c->plan.esz, (cplx*)out);
+    return TTN_OK;
+}
+
+ttn_status ttn_get_state(ttn_ctx* c, ttn_c128* tensors, int64_t* offsets) {
+    if (!c || !tensors || !offsets) return TTN_E_INVALID;
+    cudaSetDevice(c->device);
+    std::vector<char> raw(c->plan.bond_off);
+    CK(cudaMemcpyAsync(raw.data(), c->d_state, raw.size(), cudaMemcpyDeviceToHost, c->stream), "state copy");
+    CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+    int64_t o = 0;
+    for (int z = 0; z < c->tree.n; ++z) {
+        offsets[z] = o;
+        std::memcpy(tensors + o, raw.data() + c->plan.tensor_off[z], c->tree.size[z] * 16);
+        o += c->tree.size[z];
+    }
+    offsets[c->tree.n] = o;
+    return TTN_OK;
+}
+
+ttn_status ttn_bond_dims(ttn_ctx* c, int* out) {
+    if (!c || !out) return TTN_E_INVALID;
+    for (int z = 0; z < c->tree.n; ++z) out[z] = z == 0 ? 1 : c->tree.bond[z];
+    return TTN_OK;
+}
+
+ttn_status ttn_set_stream(ttn_ctx* c, void* stream) {
+    if (!c) return TTN_E_INVALID;
+    c->stream = (cudaStream_t)stream;
+    return TTN_OK;
+}
+
+ttn_status ttn_device_bytes(const ttn_ctx* c, size_t* bytes) {
+    if (!c || !bytes) return TTN_E_INVALID;
+    *bytes = c->state_bytes + c->ops_bytes;
+    return TTN_OK;
+}
+
+const char* ttn_last_error(const ttn_ctx* c) {
+    if (!c) return g_create_error.c_str();
+    return c->err.c_str();
+}
+
+void ttn_destroy(ttn_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_ops(c);
+    if (c->d_state) cudaFree(c->d_state);
+    if (c->d_batch) cudaFree(c->d_batch);
+    delete c;
+}
+
+}  // extern "C"

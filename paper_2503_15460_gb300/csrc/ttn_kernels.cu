@@ -1,0 +1,679 @@
+// libttn device code: the sweep interpreter and its building blocks.
+//
+// One thread block executes the whole op list of one TTN instance (a node
+// update is a dependent chain of small contractions, so the work of one
+// instance stays on one SM and instances run side by side).  All
+// operations below are written for the whole block; __syncthreads()
+// separates dependent phases.
+//
+// T is the bulk element type: double2 (complex128 mode) or float2 (mixed
+// mode).  Scalars that steer the algorithm -- Krylov coefficients, norms,
+// the small projected exponential, Householder scalars -- are FP64 in both
+// modes, and the QR works on an FP64 copy of the matricised tensor.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ttn_program.h"
+#include "ttn_launch.h"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+// ---------------------------------------------------------------------------
+// complex helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double2 cd(double2 a) { return a; }
+__device__ __forceinline__ double2 cd(float2 a) { return make_double2(a.x, a.y); }
+template <class T> __device__ __forceinline__ T cT(double2 a);
+template <> __device__ __forceinline__ double2 cT<double2>(double2 a) { return a; }
+template <> __device__ __forceinline__ float2 cT<float2>(double2 a) { return make_float2((float)a.x, (float)a.y); }
+
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cconjmul(double2 a, double2 b) {   // conj(a) * b
+    return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+    double den = b.x * b.x + b.y * b.y;
+    return make_double2((a.x * b.x + a.y * b.y) / den, (a.y * b.x - a.x * b.y) / den);
+}
+
+// bulk multiply-accumulate in the element type's precision
+__device__ __forceinline__ void cfma(double2& acc, double2 a, double2 b) {
+    acc.x = fma(a.x, b.x, acc.x); acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y); acc.y = fma(a.y, b.x, acc.y);
+}
+__device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
+    acc.x = fmaf(a.x, b.x, acc.x); acc.x = fmaf(-a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y); acc.y = fmaf(a.y, b.x, acc.y);
+}
+template <class T> __device__ __forceinline__ T czero();
+template <> __device__ __forceinline__ double2 czero<double2>() { return make_double2(0.0, 0.0); }
+template <> __device__ __forceinline__ float2 czero<float2>() { return make_float2(0.f, 0.f); }
+
+__device__ __forceinline__ double2 warp_sum(double2 v) {
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// shared scratch
+// ---------------------------------------------------------------------------
+struct Smem {
+    double2 H[(TTN_KMAX + 1) * TTN_KMAX];   // projected matrix, row-major, ld TTN_KMAX
+    double2 y[TTN_KMAX + 1];
+    double2 u[TTN_KMAX + 1];
+    double2 dots[TTN_KMAX + 1];
+    double2 red[kWarps];
+    double2 bc[4];
+    double2 qtau[TTN_MAXCHI];
+    int qskip[TTN_MAXCHI];
+    double qsign[TTN_MAXCHI];
+    int flag;
+};
+
+__device__ double2 block_sum(double2 v, Smem& sm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) sm.red[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        double2 w = lane < kWarps ? sm.red[lane] : make_double2(0.0, 0.0);
+        w = warp_sum(w);
+        if (lane == 0) sm.bc[0] = w;
+    }
+    __syncthreads();
+    double2 r = sm.bc[0];
+    __syncthreads();
+    return r;
+}
+
+template <class T>
+__device__ double2 block_dot(const T* __restrict__ a, const T* __restrict__ b, int64_t n, Smem& sm) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int64_t i = threadIdx.x; i < n; i += kThreads) acc = cadd(acc, cconjmul(cd(a[i]), cd(b[i])));
+    return block_sum(acc, sm);
+}
+
+// ---------------------------------------------------------------------------
+// tensor primitives
+// ---------------------------------------------------------------------------
+struct Shape {
+    int D;
+    int d[TTN_MAXD];
+    __device__ int64_t size() const { int64_t s = 1; for (int j = 0; j < D; ++j) s *= d[j]; return s; }
+    __device__ int64_t before(int k) const { int64_t s = 1; for (int j = 0; j < k; ++j) s *= d[j]; return s; }
+    __device__ int64_t after(int k) const { int64_t s = 1; for (int j = k + 1; j < D; ++j) s *= d[j]; return s; }
+};
+
+// out[l, p, r] (+)= w * sum_m M[p, m] in[l, m, r]   (M: nout x nin, or its
+// transpose stored nin x nout when transM)
+template <class T>
+__device__ void mode_prod(T* __restrict__ out, const T* __restrict__ in, int64_t L, int nin, int nout,
+                          int64_t R, const T* __restrict__ M, bool transM, double2 w, bool accumulate) {
+    const int64_t total = L * nout * R;
+    const T wt = cT<T>(w);
+    for (int64_t idx = threadIdx.x; idx < total; idx += kThreads) {
+        const int64_t r = idx % R;
+        const int64_t t = idx / R;
+        const int p = (int)(t % nout);
+        const int64_t l = t / nout;
+        const T* src = in + l * nin * R + r;
+        T acc = czero<T>();
+        if (transM) {
+            for (int m = 0; m < nin; ++m) cfma(acc, M[m * nout + p], src[m * R]);
+        } else {
+            const T* row = M + p * nin;
+            for (int m = 0; m < nin; ++m) cfma(acc, row[m], src[m * R]);
+        }
+        T v = czero<T>();
+        cfma(v, wt, acc);
+        if (accumulate) { T o = out[idx]; o.x += v.x; o.y += v.y; out[idx] = o; }
+        else out[idx] = v;
+    }
+}
+
+template <class T>
+__device__ void copy_vec(T* __restrict__ dst, const T* __restrict__ src, int64_t n) {
+    for (int64_t i = threadIdx.x; i < n; i += kThreads) dst[i] = src[i];
+}
+
+// Chain of mode products of one entry over the modes != skip (skip = -1:
+// all modes).  Returns the buffer holding the result (src itself if the
+// entry has no factor there).  The last factor is written to `last_out`
+// with weight w (accumulate) when last_out != nullptr.
+template <class T>
+__device__ const T* apply_chain(const T* src, T* t1, T* t2, const Shape& sh, const TtnEntry& e,
+                                const TtnSlot* slots, int skip, T* last_out, double2 w) {
+    int modes[TTN_MAXD], nf = 0;
+    for (int j = 0; j < sh.D; ++j)
+        if (j != skip && e.slot[j] >= 0) modes[nf++] = j;
+    const T* cur = src;
+    for (int f = 0; f < nf; ++f) {
+        const int j = modes[f];
+        const TtnSlot s = slots[e.slot[j]];
+        const T* M = (const T*)s.ptr;
+        const int64_t L = sh.before(j), R = sh.after(j);
+        const int n = sh.d[j];
+        if (f == nf - 1 && last_out) {
+            mode_prod(last_out, cur, L, n, n, R, M, false, w, true);
+            __syncthreads();
+            return last_out;
+        }
+        T* dst = (cur == t1) ? t2 : t1;
+        mode_prod(dst, cur, L, n, n, R, M, false, make_double2(1.0, 0.0), false);
+        __syncthreads();
+        cur = dst;
+    }
+    return cur;
+}
+
+// out = sum_e w_e (x_j M_ej) in   (effective Hamiltonian / bond operator)
+template <class T>
+__device__ void heff_apply(T* __restrict__ out, const T* __restrict__ in, T* t1, T* t2, const Shape& sh,
+                           const TtnEntry* es, int ne, const TtnSlot* slots) {
+    const int64_t S = sh.size();
+    for (int64_t i = threadIdx.x; i < S; i += kThreads) out[i] = czero<T>();
+    __syncthreads();
+    for (int ei = 0; ei < ne; ++ei) {
+        const TtnEntry e = es[ei];
+        const double2 w = make_double2(e.wr, e.wi);
+        bool any = false;
+        for (int j = 0; j < sh.D; ++j) any |= e.slot[j] >= 0;
+        if (!any) {
+            const T wt = cT<T>(w);
+            for (int64_t i = threadIdx.x; i < S; i += kThreads) {
+                T o = out[i]; cfma(o, wt, in[i]); out[i] = o;
+            }
+            __syncthreads();
+            continue;
+        }
+        apply_chain(in, t1, t2, sh, e, slots, -1, out, w);
+    }
+}
+
+// G[a, b] += w * sum_{other indices} conj(X[.., a, ..]) Y[.., b, ..]   (index k kept)
+template <class T>
+__device__ void gram_acc(T* G, const T* __restrict__ X, const T* __restrict__ Y, const Shape& sh, int k, double2 w) {
+    const int chi = sh.d[k];
+    const int64_t L = sh.before(k), R = sh.after(k), O = L * R;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int pr = warp; pr < chi * chi; pr += kWarps) {
+        const int a = pr / chi, b = pr % chi;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int64_t o = lane; o < O; o += 32) {
+            const int64_t l = o / R, r = o % R;
+            acc = cadd(acc, cconjmul(cd(X[(l * chi + a) * R + r]), cd(Y[(l * chi + b) * R + r])));
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) {
+            double2 g = cd(G[a * chi + b]);
+            G[a * chi + b] = cT<T>(cadd(g, cmul(w, acc)));
+        }
+    }
+}
+
+// Environment build: for every entry, out += w * Q^dag (x_{j != keep} M_j) Q.
+template <class T>
+__device__ void env_build(const T* Q, T* t1, T* t2, const Shape& sh, int keep, const TtnEntry* es, int ne,
+                          const TtnSlot* slots) {
+    int prev = -1;
+    for (int ei = 0; ei < ne; ++ei) {
+        const TtnEntry e = es[ei];
+        T* out = (T*)slots[e.out].ptr;
+        if (e.out != prev) {
+            const int n = slots[e.out].rows * slots[e.out].cols;
+            for (int i = threadIdx.x; i < n; i += kThreads) out[i] = czero<T>();
+            __syncthreads();
+            prev = e.out;
+        }
+        const T* Y = apply_chain(Q, t1, t2, sh, e, slots, keep, (T*)nullptr, make_double2(1.0, 0.0));
+        gram_acc(out, Q, Y, sh, keep, make_double2(e.wr, e.wi));
+        __syncthreads();
+    }
+}
+
+// out = sum w * M  (slot[0] = -1: w * identity)
+template <class T>
+__device__ void combo(const TtnEntry* es, int ne, const TtnSlot* slots) {
+    int prev = -1;
+    for (int ei = 0; ei < ne; ++ei) {
+        const TtnEntry e = es[ei];
+        T* out = (T*)slots[e.out].ptr;
+        const int n = slots[e.out].rows;
+        if (e.out != prev) {
+            for (int i = threadIdx.x; i < n * n; i += kThreads) out[i] = czero<T>();
+            __syncthreads();
+            prev = e.out;
+        }
+        const double2 w = make_double2(e.wr, e.wi);
+        const T* M = e.slot[0] >= 0 ? (const T*)slots[e.slot[0]].ptr : nullptr;
+        for (int i = threadIdx.x; i < n * n; i += kThreads) {
+            double2 m = M ? cd(M[i]) : make_double2((i / n == i % n) ? 1.0 : 0.0, 0.0);
+            out[i] = cT<T>(cadd(cd(out[i]), cmul(w, m)));
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Householder QR of the matricisation with index k as the column index.
+// A is overwritten by Q; R (n x n, FP64) is left in Wc's upper triangle with
+// signs in sm.qsign.  Rank-deficient columns (remainder norm <= tol ||A||_F)
+// get the identity reflector, as in the oracle's definition.
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ void qr_mode(T* A, const Shape& sh, int k, double2* Wc, double2* Qc, double tol, Smem& sm) {
+    const int n = sh.d[k];
+    const int64_t L = sh.before(k), R = sh.after(k), m = L * R, S = m * n;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // gather column-major: Wc[j*m + (l*R + r)] = A[(l*n + j)*R + r]
+    double2 part = make_double2(0.0, 0.0);
+    for (int64_t idx = threadIdx.x; idx < S; idx += kThreads) {
+        const int64_t j = idx / m, I = idx % m;
+        const int64_t l = I / R, r = I % R;
+        double2 v = cd(A[(l * n + j) * R + r]);
+        Wc[idx] = v;
+        part.x += cabs2(v);
+    }
+    const double thr = tol * sqrt(block_sum(part, sm).x);
+    for (int j = 0; j < n; ++j) {
+        double2* x = Wc + (int64_t)j * m;
+        double2 s = make_double2(0.0, 0.0);
+        for (int64_t i = j + threadIdx.x; i < m; i += kThreads) s.x += cabs2(x[i]);
+        const double nrm = sqrt(block_sum(s, sm).x);
+        const double2 alpha = x[j];
+        if (nrm <= thr) {
+            for (int64_t i = j + 1 + threadIdx.x; i < m; i += kThreads) x[i] = make_double2(0.0, 0.0);
+            if (threadIdx.x == 0) { sm.qskip[j] = 1; sm.qtau[j] = make_double2(0.0, 0.0); }
+            __syncthreads();
+            continue;
+        }
+        const double beta = alpha.x >= 0.0 ? -nrm : nrm;
+        const double2 tau = cscale(csub(make_double2(beta, 0.0), alpha), 1.0 / beta);
+        const double2 scl = cdiv(make_double2(1.0, 0.0), csub(alpha, make_double2(beta, 0.0)));
+        for (int64_t i = j + 1 + threadIdx.x; i < m; i += kThreads) x[i] = cmul(x[i], scl);
+        __syncthreads();
+        if (threadIdx.x == 0) { x[j] = make_double2(beta, 0.0); sm.qskip[j] = 0; sm.qtau[j] = tau; }
+        const double2 ctau = make_double2(tau.x, -tau.y);
+        for (int c = j + 1 + warp; c < n; c += kWarps) {
+            double2* y = Wc + (int64_t)c * m;
+            double2 acc = make_double2(0.0, 0.0);
+            for (int64_t i = j + lane; i < m; i += 32) {
+                double2 v = (i == j) ? make_double2(1.0, 0.0) : x[i];
+                acc = cadd(acc, cconjmul(v, y[i]));
+            }
+            acc = warp_sum(acc);
+            const double2 f = cmul(ctau, acc);
+            for (int64_t i = j + lane; i < m; i += 32) {
+                double2 v = (i == j) ? make_double2(1.0, 0.0) : x[i];
+                y[i] = csub(y[i], cmul(v, f));
+            }
+        }
+        __syncthreads();
+    }
+    // Q = H_0 .. H_{n-1} I[:, :n]
+    for (int64_t idx = threadIdx.x; idx < S; idx += kThreads) {
+        const int64_t c = idx / m, i = idx % m;
+        Qc[idx] = make_double2(i == c ? 1.0 : 0.0, 0.0);
+    }
+    __syncthreads();
+    for (int j = n - 1; j >= 0; --j) {
+        if (sm.qskip[j]) continue;
+        const double2 tau = sm.qtau[j];
+        const double2* x = Wc + (int64_t)j * m;
+        for (int c = j + warp; c < n; c += kWarps) {
+            double2* y = Qc + (int64_t)c * m;
+            double2 acc = make_double2(0.0, 0.0);
+            for (int64_t i = j + lane; i < m; i += 32) {
+                double2 v = (i == j) ? make_double2(1.0, 0.0) : x[i];
+                acc = cadd(acc, cconjmul(v, y[i]));
+            }
+            acc = warp_sum(acc);
+            const double2 f = cmul(tau, acc);
+            for (int64_t i = j + lane; i < m; i += 32) {
+                double2 v = (i == j) ? make_double2(1.0, 0.0) : x[i];
+                y[i] = csub(y[i], cmul(v, f));
+            }
+        }
+        __syncthreads();
+    }
+    // signs: diag(R) real >= 0
+    for (int j = threadIdx.x; j < n; j += kThreads)
+        sm.qsign[j] = (!sm.qskip[j] && Wc[(int64_t)j * m + j].x < 0.0) ? -1.0 : 1.0;
+    __syncthreads();
+    for (int64_t idx = threadIdx.x; idx < S; idx += kThreads) {
+        const int64_t j = idx / m, I = idx % m;
+        const int64_t l = I / R, r = I % R;
+        A[(l * n + j) * R + r] = cT<T>(cscale(Qc[idx], sm.qsign[j]));
+    }
+    __syncthreads();
+}
+
+// R[a][b] of the last QR (a <= b), sign-fixed
+__device__ __forceinline__ double2 qr_R(const double2* Wc, int64_t m, int a, int b, const Smem& sm) {
+    if (a > b) return make_double2(0.0, 0.0);
+    return cscale(Wc[(int64_t)b * m + a], sm.qsign[a]);
+}
+
+// ---------------------------------------------------------------------------
+// Small projected exponential: sm.y = exp(-i tau H_m) e_0 (warp 0).
+// Scaling into substeps of 1-norm <= 1/2, each summed as a Taylor series on
+// the vector (Moler & Van Loan, "Nineteen dubious ways", method 1 with
+// scaling); for a tridiagonal H only the band is used.
+// ---------------------------------------------------------------------------
+__device__ void small_expm(Smem& sm, int m, double tau, bool band) {
+    if ((threadIdx.x >> 5) != 0) return;
+    const int i = threadIdx.x & 31;
+    double colsum = 0.0;
+    if (i < m)
+        for (int r = 0; r < m; ++r) colsum += sqrt(cabs2(sm.H[r * TTN_KMAX + i]));
+    const double nrm = warp_max(colsum) * fabs(tau);
+    if (!(nrm <= 1e5)) {            // not finite or absurdly stiff: report NaN, caller fails
+        if (i < m) sm.y[i] = make_double2(NAN, NAN);
+        __syncwarp();
+        return;
+    }
+    int s = (int)ceil(nrm / 0.5);
+    if (s < 1) s = 1;
+    const double h = tau / s;
+    double2 y = make_double2(i == 0 ? 1.0 : 0.0, 0.0);
+    const int jlo = band ? max(0, i - 1) : max(0, i - 1);
+    const int jhi = band ? min(m - 1, i + 1) : m - 1;
+    for (int step = 0; step < s; ++step) {
+        double2 term = y, acc = y;
+        for (int kk = 1; kk <= 40; ++kk) {
+            if (i < TTN_KMAX + 1) sm.u[i] = term;
+            __syncwarp();
+            double2 nt = make_double2(0.0, 0.0);
+            if (i < m)
+                for (int j = jlo; j <= jhi; ++j) nt = cadd(nt, cmul(sm.H[i * TTN_KMAX + j], sm.u[j]));
+            __syncwarp();
+            // term <- (-i h / kk) * H term
+            const double f = h / kk;
+            term = make_double2(nt.y * f, -nt.x * f);
+            if (i >= m) term = make_double2(0.0, 0.0);
+            acc = cadd(acc, term);
+            const double tmax = warp_max(sqrt(cabs2(term)));
+            const double amax = warp_max(sqrt(cabs2(acc)));
+            if (tmax <= 1e-18 * amax) break;
+        }
+        y = acc;
+    }
+    if (i < m) sm.y[i] = y;
+    __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
+// Krylov exponential x <- exp(-i tau Hop) x (Lanczos when herm, Arnoldi
+// otherwise; two classical Gram-Schmidt passes against the whole basis).
+// The basis V is kept in the bulk type TB; x (node tensor or bond matrix) in
+// the state type TS.  The result is assembled as
+//     x_new = y_0 x + ||x|| sum_{i>=1} y_i V_i
+// so that the leading term keeps the state's precision.
+// Stops on Saad's estimate h_{m+1,m} |e_m^T exp(-i tau H_m) e_1| <= tol.
+// Returns 1 when converged (x updated), 0 when kmax was reached, -1 on a
+// non-finite norm.
+// ---------------------------------------------------------------------------
+template <class TS, class TB>
+__device__ int krylov_once(TS* x, const Shape& sh, const TtnEntry* es, int ne, const TtnSlot* slots,
+                           double tau, int herm, double tol, int kmax, TB* V, int64_t smax, TB* t1, TB* t2,
+                           Smem& sm) {
+    const int64_t S = sh.size();
+    double2 nb = make_double2(0.0, 0.0);
+    for (int64_t i = threadIdx.x; i < S; i += kThreads) nb.x += cabs2(cd(x[i]));
+    const double beta0 = sqrt(block_sum(nb, sm).x);
+    if (beta0 == 0.0) return 1;
+    if (!isfinite(beta0)) return -1;
+    for (int i = threadIdx.x; i < (TTN_KMAX + 1) * TTN_KMAX; i += kThreads) sm.H[i] = make_double2(0.0, 0.0);
+    {
+        const double inv = 1.0 / beta0;
+        for (int64_t i = threadIdx.x; i < S; i += kThreads) V[i] = cT<TB>(cscale(cd(x[i]), inv));
+    }
+    __syncthreads();
+    for (int j = 0; j < kmax; ++j) {
+        TB* vj = V + (int64_t)j * smax;
+        TB* w = V + (int64_t)(j + 1) * smax;
+        heff_apply(w, vj, t1, t2, sh, es, ne, slots);
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int i = 0; i <= j; ++i) {
+                double2 h = block_dot(V + (int64_t)i * smax, w, S, sm);
+                if (threadIdx.x == 0) { sm.dots[i] = h; sm.H[i * TTN_KMAX + j] = cadd(sm.H[i * TTN_KMAX + j], h); }
+            }
+            __syncthreads();
+            for (int64_t e = threadIdx.x; e < S; e += kThreads) {
+                double2 acc = cd(w[e]);
+                for (int i = 0; i <= j; ++i) acc = csub(acc, cmul(sm.dots[i], cd(V[(int64_t)i * smax + e])));
+                w[e] = cT<TB>(acc);
+            }
+            __syncthreads();
+        }
+        if (herm && threadIdx.x == 0) {
+            sm.H[j * TTN_KMAX + j].y = 0.0;
+            for (int i = 0; i + 1 < j; ++i) sm.H[i * TTN_KMAX + j] = make_double2(0.0, 0.0);
+            if (j > 0) sm.H[(j - 1) * TTN_KMAX + j] = sm.H[j * TTN_KMAX + (j - 1)];
+        }
+        double2 nw = make_double2(0.0, 0.0);
+        for (int64_t e = threadIdx.x; e < S; e += kThreads) nw.x += cabs2(cd(w[e]));
+        const double hnext = sqrt(block_sum(nw, sm).x);
+        if (threadIdx.x == 0) sm.H[(j + 1) * TTN_KMAX + j] = make_double2(hnext, 0.0);
+        __syncthreads();
+        const int mm = j + 1;
+        small_expm(sm, mm, tau, herm != 0);
+        __syncthreads();
+        const double err = hnext * sqrt(cabs2(sm.y[j]));
+        if (!isfinite(hnext) || !isfinite(err)) return -1;
+        if (err <= tol || hnext == 0.0) {
+            const double2 y0 = sm.y[0];
+            for (int64_t e = threadIdx.x; e < S; e += kThreads) {
+                double2 acc = make_double2(0.0, 0.0);
+                for (int i = 1; i < mm; ++i) acc = cadd(acc, cmul(sm.y[i], cd(V[(int64_t)i * smax + e])));
+                x[e] = cT<TS>(cadd(cmul(y0, cd(x[e])), cscale(acc, beta0)));
+            }
+            __syncthreads();
+            return 1;
+        }
+        const double inv = 1.0 / hnext;
+        for (int64_t e = threadIdx.x; e < S; e += kThreads) w[e] = cT<TB>(cscale(cd(w[e]), inv));
+        __syncthreads();
+    }
+    return 0;
+}
+
+template <class TS, class TB>
+__device__ int krylov_expm(TS* x, const Shape& sh, const TtnEntry* es, int ne, const TtnSlot* slots,
+                           double tau, int herm, double tol, int kmax, TB* V, int64_t smax, TB* t1, TB* t2,
+                           Smem& sm) {
+    // substeps: halve the interval whenever kmax is reached (at most 2^12 pieces)
+    int nsub = 1, done = 0;
+    while (done < nsub) {
+        const int r = krylov_once(x, sh, es, ne, slots, tau / nsub, herm, tol, kmax, V, smax, t1, t2, sm);
+        if (r < 0) return 0;
+        if (r > 0) {
+            ++done;
+        } else {
+            if (nsub >= (1 << 12)) return 0;
+            nsub *= 2; done *= 2;
+        }
+    }
+    return 1;
+}
+
+template <class TB, class TS>
+__device__ const TB* as_bulk(const TS* a, TB* buf, int64_t n) {
+    if (sizeof(TS) == sizeof(TB)) return (const TB*)a;
+    for (int64_t i = threadIdx.x; i < n; i += kThreads) buf[i] = cT<TB>(cd(a[i]));
+    __syncthreads();
+    return buf;
+}
+
+// ---------------------------------------------------------------------------
+// interpreter: TS = node tensor / bond type, TB = bulk type
+// ---------------------------------------------------------------------------
+template <class TS, class TB>
+__device__ void run_op(const TtnOp& op, const TtnInstance& in, double dt, Smem& sm) {
+    Shape sh;
+    sh.D = op.D;
+    for (int j = 0; j < TTN_MAXD; ++j) sh.d[j] = j < op.D ? op.dims[j] : 1;
+    TB* work = (TB*)in.work;
+    TB* V = work;
+    TB* t3 = work + (int64_t)TTN_KMAX * in.smax;        // last basis vector: free outside EVOLVE
+    TB* t1 = work + (int64_t)(TTN_KMAX + 1) * in.smax;
+    TB* t2 = t1 + in.smax;
+    double2* Wc = (double2*)(t2 + in.smax);
+    double2* Qc = Wc + in.smax;
+    const TtnEntry* es = in.entries + op.e0;
+    switch (op.type) {
+    case TTN_OP_QR_DOWN: {
+        TS* A = (TS*)op.a;
+        TS* B = (TS*)op.b;
+        qr_mode(A, sh, op.k, Wc, Qc, in.qtol, sm);
+        const int n = sh.d[op.k];
+        const int64_t m = sh.size() / n;
+        for (int i = threadIdx.x; i < n * n; i += kThreads) {   // B = R^T
+            const int a = i / n, b = i % n;
+            B[i] = cT<TS>(qr_R(Wc, m, b, a, sm));
+        }
+        __syncthreads();
+        break;
+    }
+    case TTN_OP_QR_UP: {
+        TS* A = (TS*)op.a;
+        TS* B = (TS*)op.b;
+        qr_mode(A, sh, op.k, Wc, Qc, in.qtol, sm);
+        const int n = sh.d[op.k];
+        const int64_t m = sh.size() / n;
+        for (int i = threadIdx.x; i < n * n; i += kThreads) {   // B = R
+            const int a = i / n, b = i % n;
+            B[i] = cT<TS>(qr_R(Wc, m, a, b, sm));
+        }
+        __syncthreads();
+        break;
+    }
+    case TTN_OP_ABSORB_CHILD: {      // A <- A x_last B^T
+        TS* A = (TS*)op.a;
+        const TS* B = (const TS*)op.b;
+        TS* tmp = (TS*)Qc;
+        const int n = sh.d[op.k];
+        mode_prod(tmp, A, sh.before(op.k), n, n, (int64_t)1, B, true, make_double2(1.0, 0.0), false);
+        __syncthreads();
+        copy_vec(A, (const TS*)tmp, sh.size());
+        __syncthreads();
+        break;
+    }
+    case TTN_OP_ABSORB_PARENT: {     // A <- B x_k A
+        TS* A = (TS*)op.a;
+        const TS* B = (const TS*)op.b;
+        TS* tmp = (TS*)Qc;
+        const int n = sh.d[op.k];
+        mode_prod(tmp, A, sh.before(op.k), n, n, sh.after(op.k), B, false, make_double2(1.0, 0.0), false);
+        __syncthreads();
+        copy_vec(A, (const TS*)tmp, sh.size());
+        __syncthreads();
+        break;
+    }
+    case TTN_OP_ENV: {
+        const TB* Q = as_bulk<TB>((const TS*)op.a, t3, sh.size());
+        env_build(Q, t1, t2, sh, op.k, es, op.ne, in.slots);
+        break;
+    }
+    case TTN_OP_COMBO:
+        combo<TB>(es, op.ne, in.slots);
+        break;
+    case TTN_OP_EVOLVE: {
+        const int ok = krylov_expm((TS*)op.a, sh, es, op.ne, in.slots, op.tau_coef * dt, op.hermitian, in.ktol,
+                                   in.kmax, V, in.smax, t1, t2, sm);
+        if (!ok && threadIdx.x == 0) atomicExch(in.status, 4);   // TTN_E_NOCONV
+        __syncthreads();
+        break;
+    }
+    case TTN_OP_DOT: {
+        double2 r;
+        if (op.ne > 0) {
+            const TB* A = as_bulk<TB>((const TS*)op.a, t3, sh.size());
+            heff_apply(t1, A, t2, V, sh, es, op.ne, in.slots);
+            r = block_dot(A, t1, sh.size(), sm);
+        } else {
+            const TS* A = (const TS*)op.a;
+            r = block_dot(A, A, sh.size(), sm);
+        }
+        if (threadIdx.x == 0) { op.out[0] = r.x; op.out[1] = r.y; }
+        __syncthreads();
+        break;
+    }
+    case TTN_OP_CONTRACT_VEC: {      // chain of rectangular mode products, result into slot k
+        const TtnEntry e = es[0];
+        const TB* cur = as_bulk<TB>((const TS*)op.a, t3, sh.size());
+        Shape s2 = sh;
+        for (int j = 0; j < sh.D; ++j) {
+            if (e.slot[j] < 0) continue;
+            const TtnSlot s = in.slots[e.slot[j]];
+            TB* dst = (cur == t1) ? t2 : t1;
+            mode_prod(dst, cur, s2.before(j), s.cols, s.rows, s2.after(j), (const TB*)s.ptr, false,
+                      make_double2(1.0, 0.0), false);
+            __syncthreads();
+            s2.d[j] = s.rows;
+            cur = dst;
+        }
+        copy_vec((TB*)in.slots[op.k].ptr, cur, s2.size());
+        __syncthreads();
+        break;
+    }
+    case TTN_OP_STEP_END:
+        if (threadIdx.x == 0) {
+            const int s = *in.steps_done;
+            if (in.stamps) {
+                unsigned long long t;
+                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+                in.stamps[s & 4095] = t;
+            }
+            *in.steps_done = s + 1;
+        }
+        __syncthreads();
+        break;
+    default:
+        if (threadIdx.x == 0) atomicExch(in.status, 6);
+        __syncthreads();
+        break;
+    }
+}
+
+template <class TS, class TB>
+__global__ void __launch_bounds__(kThreads) program_kernel(const TtnInstance* insts, int n_inst, double dt, int nrep) {
+    __shared__ Smem sm;
+    const int b = blockIdx.x;
+    if (b >= n_inst) return;
+    const TtnInstance in = insts[b];
+    for (int rep = 0; rep < nrep; ++rep) {
+        for (int o = 0; o < in.n_ops; ++o) {
+            if (threadIdx.x == 0) sm.flag = *((volatile int*)in.status);
+            __syncthreads();
+            if (sm.flag != 0) return;
+            const TtnOp op = in.ops[o];
+            run_op<TS, TB>(op, in, dt, sm);
+        }
+    }
+}
+
+}  // namespace
+
+int ttn_launch_program(int precision, const TtnInstance* d_insts, int n_inst, double dt, int nrep, cudaStream_t s) {
+    if (n_inst <= 0) return 0;
+    if (precision == 0) program_kernel<double2, double2><<<n_inst, kThreads, 0, s>>>(d_insts, n_inst, dt, nrep);
+    else program_kernel<double2, float2><<<n_inst, kThreads, 0, s>>>(d_insts, n_inst, dt, nrep);
+    return (int)cudaGetLastError();
+}

@@ -1,0 +1,789 @@
+// Host-side planning for libttn (see ttn_plan.hpp).
+//
+// Operator grouping.  For the bond between node c and its parent, every SOP
+// term r (paper Eq. sop_ham) splits into the factors inside the subtree of c
+// and the factors outside.  Following the node decomposition of Sec. II.B.1
+// (Eqs. sop_node_naive, spf_hamiltonian_op, shf_hamiltonian_op) the bond
+// carries
+//   * up channels   (single-particle operators, Sec. II.C matrices h):
+//       LOC  = sum of all terms acting only inside the subtree (one matrix),
+//       PROD = the inside part of each term that acts on both sides;
+//   * down channels (mean-field operators, matrices H):
+//       LOC  = sum of all terms acting only outside the subtree,
+//       PROD = the outside part of each term that acts on both sides.
+// Each channel's matrix at a node is a sum of products of its children's
+// channels, which is what the environment builds evaluate.  Identity
+// factors are skipped (the copy optimisation the paper describes for the
+// hierarchical SOP form); the result is exactly the plain SOP operator.
+#include "ttn_plan.hpp"
+
+#include <algorithm>
+#include <cstring>
+#include <cmath>
+#include <functional>
+#include <set>
+#include <sstream>
+
+namespace ttn {
+
+namespace {
+
+int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+std::vector<int> Tree::preorder() const {
+    std::vector<int> out;
+    std::vector<int> st{0};
+    while (!st.empty()) {
+        int z = st.back(); st.pop_back();
+        out.push_back(z);
+        for (int i = (int)ch[z].size() - 1; i >= 0; --i) st.push_back(ch[z][i]);
+    }
+    return out;
+}
+
+std::vector<int> Tree::postorder() const {
+    std::vector<int> out;
+    std::function<void(int)> rec = [&](int z) {
+        for (int c : ch[z]) rec(c);
+        out.push_back(z);
+    };
+    rec(0);
+    return out;
+}
+
+std::string build_tree(int n, const int* parent, const int* phys, const int* bond, Tree& t) {
+    std::ostringstream err;
+    if (n < 1 || n > 65535) return "n_nodes must be in 1..65535";
+    if (!parent || !phys || !bond) return "null tree array";
+    t = Tree();
+    t.n = n;
+    t.parent.assign(parent, parent + n);
+    t.phys.assign(phys, phys + n);
+    t.bond.assign(bond, bond + n);
+    t.ch.assign(n, {});
+    if (t.parent[0] != -1) return "parent[0] must be -1";
+    for (int i = 1; i < n; ++i) {
+        if (t.parent[i] < 0 || t.parent[i] >= i) {
+            err << "parent[" << i << "] = " << t.parent[i] << " must be in [0, " << i << ")";
+            return err.str();
+        }
+        t.ch[t.parent[i]].push_back(i);
+    }
+    t.bond[0] = 1;
+    for (int z = 0; z < n; ++z) {
+        if (t.phys[z] < 0) return "negative phys_dim";
+        if (t.phys[z] > 0 && !t.ch[z].empty()) { err << "node " << z << " has children and phys_dim > 0"; return err.str(); }
+        if (t.phys[z] == 0 && t.ch[z].empty()) { err << "interior node " << z << " has no children"; return err.str(); }
+        if (t.phys[z] > TTN_MAXCHI) { err << "phys_dim of node " << z << " exceeds " << TTN_MAXCHI; return err.str(); }
+        if (z > 0 && (t.bond[z] < 1 || t.bond[z] > TTN_MAXCHI)) { err << "bond_dim of node " << z << " must be in 1.." << TTN_MAXCHI; return err.str(); }
+        if ((int)t.ch[z].size() + 1 > TTN_MAXD) { err << "node " << z << " has more than " << TTN_MAXD - 1 << " children"; return err.str(); }
+    }
+    t.dims.assign(n, {});
+    t.size.assign(n, 0);
+    for (int z = 0; z < n; ++z) {
+        if (t.leaf(z)) t.dims[z].push_back(t.phys[z]);
+        else for (int c : t.ch[z]) t.dims[z].push_back(t.bond[c]);
+        t.dims[z].push_back(z == 0 ? 1 : t.bond[z]);
+        int64_t s = 1;
+        for (int d : t.dims[z]) s *= d;
+        t.size[z] = s;
+        if (s > (int64_t(1) << 28)) { err << "tensor of node " << z << " is too large"; return err.str(); }
+        // every matricisation used by the sweep needs rows >= columns
+        for (size_t k = 0; k < t.dims[z].size(); ++k) {
+            if (z == 0 && k + 1 == t.dims[z].size()) continue;   // root's dummy index
+            if (t.leaf(z) && k == 0) continue;                   // a leaf is never split along its physical index
+            if (s / t.dims[z][k] < t.dims[z][k]) {
+                err << "node " << z << ": index " << k << " of dimension " << t.dims[z][k]
+                    << " exceeds the product " << s / t.dims[z][k] << " of the other indices";
+                return err.str();
+            }
+        }
+    }
+    // Euler tour
+    t.tin.assign(n, 0); t.tout.assign(n, 0);
+    int clock = 0;
+    std::function<void(int)> rec = [&](int z) {
+        t.tin[z] = clock++;
+        for (int c : t.ch[z]) rec(c);
+        t.tout[z] = clock;
+    };
+    rec(0);
+    return "";
+}
+
+std::string build_hamiltonian(const Tree& t, int n_terms, const cplx* coeff, const int* term_ptr,
+                              const int* factor_leaf, const cplx* mats, const int64_t* mat_off,
+                              int hermitian, Hamiltonian& h) {
+    std::ostringstream err;
+    if (n_terms < 1) return "n_terms must be >= 1";
+    if (!coeff || !term_ptr) return "null coefficient / term_ptr";
+    if (term_ptr[0] != 0) return "term_ptr[0] must be 0";
+    h = Hamiltonian();
+    h.hermitian = hermitian != 0;
+    std::map<std::pair<int, std::vector<double>>, int> dedup;
+    for (int r = 0; r < n_terms; ++r) {
+        if (term_ptr[r + 1] < term_ptr[r]) return "term_ptr must be non-decreasing";
+        if (!std::isfinite(coeff[r].real()) || !std::isfinite(coeff[r].imag())) return "non-finite coefficient";
+        Key key;
+        for (int f = term_ptr[r]; f < term_ptr[r + 1]; ++f) {
+            int l = factor_leaf[f];
+            if (l < 0 || l >= t.n || !t.leaf(l)) { err << "factor " << f << " acts on node " << l << ", which is not a leaf"; return err.str(); }
+            int d = t.phys[l];
+            std::vector<double> raw(2 * d * d);
+            for (int i = 0; i < d * d; ++i) {
+                cplx v = mats[mat_off[f] + i];
+                if (!std::isfinite(v.real()) || !std::isfinite(v.imag())) return "non-finite factor matrix entry";
+                raw[2 * i] = v.real(); raw[2 * i + 1] = v.imag();
+            }
+            auto it = dedup.find({d, raw});
+            int id;
+            if (it == dedup.end()) {
+                id = (int)h.mats.size();
+                h.mats.emplace_back(mats + mat_off[f], mats + mat_off[f] + d * d);
+                h.mat_dim.push_back(d);
+                dedup[{d, raw}] = id;
+            } else id = it->second;
+            key.push_back({l, id});
+        }
+        std::sort(key.begin(), key.end());
+        for (size_t i = 1; i < key.size(); ++i)
+            if (key[i].first == key[i - 1].first) { err << "term " << r << " has two factors on leaf " << key[i].first; return err.str(); }
+        if (coeff[r] == cplx(0.0)) continue;
+        h.coeff.push_back(coeff[r]);
+        h.terms.push_back(key);
+    }
+    if (h.coeff.empty()) { h.coeff.push_back(0.0); h.terms.push_back({}); }
+    return "";
+}
+
+// ---------------------------------------------------------------------------
+// Operator planning
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Proto {
+    cplx w;
+    int out;
+    std::vector<int> slot;
+};
+
+struct Builder {
+    const Tree& t;
+    const Hamiltonian* h;
+    Plan& p;
+    std::vector<int> up_loc, down_loc, phys_loc;
+    std::vector<std::map<Key, int>> up_prod, down_prod;
+    std::vector<std::map<int, int>> phys_mat;
+    int one_slot = -1;     // 1x1 matrix holding 1 (root Gram matrix)
+
+    Builder(const Tree& t_, const Hamiltonian* h_, Plan& p_) : t(t_), h(h_), p(p_) {}
+
+    int new_slot(int rows, int cols) {
+        SlotInfo s; s.rows = rows; s.cols = cols;
+        p.slots.push_back(s);
+        return (int)p.slots.size() - 1;
+    }
+    int const_slot(int rows, int cols, const std::vector<cplx>& data) {
+        int id = new_slot(rows, cols);
+        p.slots[id].constant = true;
+        p.slots[id].data = data;
+        return id;
+    }
+
+    Key restrict_to(const Key& k, int c, bool inside) const {
+        Key out;
+        for (auto& f : k) if (t.in_sub(f.first, c) == inside) out.push_back(f);
+        return out;
+    }
+    // mode of node z that leaf l falls into: child index, 0 for the leaf itself, D-1 outside
+    int mode_of(int z, int l) const {
+        int D = (int)t.dims[z].size();
+        if (!t.in_sub(l, z)) return D - 1;
+        if (t.leaf(z)) return 0;
+        for (size_t k = 0; k < t.ch[z].size(); ++k)
+            if (t.in_sub(l, t.ch[z][k])) return (int)k;
+        return -1;
+    }
+    Key restrict_mode(int z, const Key& key, int mode) const {
+        Key out;
+        for (auto& f : key) if (mode_of(z, f.first) == mode) out.push_back(f);
+        return out;
+    }
+    // slot of the up channel of mode k of node z for a (non-empty) restriction
+    int child_up(int z, int k, const Key& key) const {
+        if (t.leaf(z)) return phys_mat[z].at(key.at(0).second);
+        return up_prod[t.ch[z][k]].at(key);
+    }
+    int child_loc(int z, int k) const {
+        if (t.leaf(z)) return phys_loc[z];
+        return up_loc[t.ch[z][k]];
+    }
+
+    void make_channels() {
+        int n = t.n;
+        up_loc.assign(n, -1); down_loc.assign(n, -1); phys_loc.assign(n, -1);
+        up_prod.assign(n, {}); down_prod.assign(n, {}); phys_mat.assign(n, {});
+        if (!h) return;
+        const int R = (int)h->terms.size();
+        // physical factor matrices and per-leaf local sums
+        std::vector<std::vector<cplx>> loc_sum(n);
+        for (int r = 0; r < R; ++r) {
+            const Key& key = h->terms[r];
+            for (auto& f : key) {
+                int l = f.first, m = f.second;
+                if (!phys_mat[l].count(m)) {
+                    int d = t.phys[l];
+                    phys_mat[l][m] = const_slot(d, d, h->mats[m]);
+                }
+            }
+            if (key.size() == 1) {
+                int l = key[0].first, d = t.phys[l];
+                if (loc_sum[l].empty()) loc_sum[l].assign(d * d, 0.0);
+                for (int i = 0; i < d * d; ++i) loc_sum[l][i] += h->coeff[r] * h->mats[key[0].second][i];
+            }
+        }
+        for (int l = 0; l < n; ++l)
+            if (!loc_sum[l].empty()) phys_loc[l] = const_slot(t.phys[l], t.phys[l], loc_sum[l]);
+        // bond channels
+        for (int c = 1; c < n; ++c) {
+            int chi = t.bond[c];
+            for (int r = 0; r < R; ++r) {
+                const Key& key = h->terms[r];
+                if (key.empty()) continue;
+                Key in = restrict_to(key, c, true), out = restrict_to(key, c, false);
+                if (!in.empty() && out.empty()) {
+                    if (up_loc[c] < 0) up_loc[c] = new_slot(chi, chi);
+                } else if (in.empty() && !out.empty()) {
+                    if (down_loc[c] < 0) down_loc[c] = new_slot(chi, chi);
+                } else {
+                    if (!up_prod[c].count(in)) up_prod[c][in] = new_slot(chi, chi);
+                    if (!down_prod[c].count(out)) down_prod[c][out] = new_slot(chi, chi);
+                }
+            }
+        }
+    }
+
+    // ---- entry lists --------------------------------------------------------
+    std::vector<Proto> up_build(int z) {
+        std::vector<Proto> es;
+        int D = (int)t.dims[z].size();
+        auto blank = [&](int out) { Proto e; e.w = 1.0; e.out = out; e.slot.assign(D, -1); return e; };
+        if (up_loc[z] >= 0) {
+            if (t.leaf(z)) {
+                Proto e = blank(up_loc[z]); e.slot[0] = phys_loc[z]; es.push_back(e);
+            } else {
+                for (size_t k = 0; k < t.ch[z].size(); ++k)
+                    if (up_loc[t.ch[z][k]] >= 0) { Proto e = blank(up_loc[z]); e.slot[k] = up_loc[t.ch[z][k]]; es.push_back(e); }
+                for (size_t r = 0; r < h->terms.size(); ++r) {
+                    const Key& key = h->terms[r];
+                    if (key.empty() || !std::all_of(key.begin(), key.end(), [&](auto& f) { return t.in_sub(f.first, z); })) continue;
+                    std::set<int> modes;
+                    for (auto& f : key) modes.insert(mode_of(z, f.first));
+                    if (modes.size() < 2) continue;
+                    Proto e = blank(up_loc[z]); e.w = h->coeff[r];
+                    for (int k : modes) e.slot[k] = child_up(z, k, restrict_mode(z, key, k));
+                    es.push_back(e);
+                }
+            }
+        }
+        for (auto& kv : up_prod[z]) {
+            Proto e = blank(kv.second);
+            if (t.leaf(z)) e.slot[0] = phys_mat[z].at(kv.first.at(0).second);
+            else {
+                std::set<int> modes;
+                for (auto& f : kv.first) modes.insert(mode_of(z, f.first));
+                for (int k : modes) e.slot[k] = child_up(z, k, restrict_mode(z, kv.first, k));
+            }
+            es.push_back(e);
+        }
+        return es;
+    }
+
+    std::vector<Proto> down_build(int z, int k) {
+        std::vector<Proto> es;
+        int c = t.ch[z][k];
+        int D = (int)t.dims[z].size();
+        auto blank = [&](int out) { Proto e; e.w = 1.0; e.out = out; e.slot.assign(D, -1); return e; };
+        if (down_loc[c] >= 0) {
+            if (z > 0 && down_loc[z] >= 0) { Proto e = blank(down_loc[c]); e.slot[D - 1] = down_loc[z]; es.push_back(e); }
+            for (size_t j = 0; j < t.ch[z].size(); ++j)
+                if ((int)j != k && up_loc[t.ch[z][j]] >= 0) { Proto e = blank(down_loc[c]); e.slot[j] = up_loc[t.ch[z][j]]; es.push_back(e); }
+            for (size_t r = 0; r < h->terms.size(); ++r) {
+                const Key& key = h->terms[r];
+                if (key.empty() || std::any_of(key.begin(), key.end(), [&](auto& f) { return t.in_sub(f.first, c); })) continue;
+                std::set<int> modes;
+                for (auto& f : key) modes.insert(mode_of(z, f.first));
+                if (modes.size() < 2) continue;
+                Proto e = blank(down_loc[c]); e.w = h->coeff[r];
+                for (int m : modes) {
+                    Key part = restrict_mode(z, key, m);
+                    e.slot[m] = (m == D - 1) ? down_prod[z].at(part) : child_up(z, m, part);
+                }
+                es.push_back(e);
+            }
+        }
+        for (auto& kv : down_prod[c]) {
+            Proto e = blank(kv.second);
+            std::set<int> modes;
+            for (auto& f : kv.first) modes.insert(mode_of(z, f.first));
+            for (int m : modes) {
+                Key part = restrict_mode(z, kv.first, m);
+                e.slot[m] = (m == D - 1) ? down_prod[z].at(part) : child_up(z, m, part);
+            }
+            es.push_back(e);
+        }
+        return es;
+    }
+
+    std::vector<Proto> heff_terms(int z) {
+        std::vector<Proto> es;
+        int D = (int)t.dims[z].size();
+        auto blank = [&]() { Proto e; e.w = 1.0; e.out = -1; e.slot.assign(D, -1); return e; };
+        int nchild = t.leaf(z) ? 1 : (int)t.ch[z].size();
+        for (int k = 0; k < nchild; ++k)
+            if (child_loc(z, k) >= 0) { Proto e = blank(); e.slot[k] = child_loc(z, k); es.push_back(e); }
+        if (z > 0 && down_loc[z] >= 0) { Proto e = blank(); e.slot[D - 1] = down_loc[z]; es.push_back(e); }
+        for (size_t r = 0; r < h->terms.size(); ++r) {
+            const Key& key = h->terms[r];
+            if (key.empty()) { Proto e = blank(); e.w = h->coeff[r]; es.push_back(e); continue; }
+            std::set<int> modes;
+            for (auto& f : key) modes.insert(mode_of(z, f.first));
+            if (modes.size() < 2) continue;
+            Proto e = blank(); e.w = h->coeff[r];
+            for (int m : modes) {
+                Key part = restrict_mode(z, key, m);
+                e.slot[m] = (m == D - 1) ? down_prod[z].at(part) : child_up(z, m, part);
+            }
+            es.push_back(e);
+        }
+        return es;
+    }
+
+    std::vector<Proto> bond_terms(int c) {
+        std::vector<Proto> es;
+        auto blank = [&]() { Proto e; e.w = 1.0; e.out = -1; e.slot.assign(2, -1); return e; };
+        if (up_loc[c] >= 0) { Proto e = blank(); e.slot[0] = up_loc[c]; es.push_back(e); }
+        if (down_loc[c] >= 0) { Proto e = blank(); e.slot[1] = down_loc[c]; es.push_back(e); }
+        for (size_t r = 0; r < h->terms.size(); ++r) {
+            const Key& key = h->terms[r];
+            if (key.empty()) { Proto e = blank(); e.w = h->coeff[r]; es.push_back(e); continue; }
+            Key in = restrict_to(key, c, true), out = restrict_to(key, c, false);
+            if (in.empty() || out.empty()) continue;
+            Proto e = blank(); e.w = h->coeff[r];
+            e.slot[0] = up_prod[c].at(in);
+            e.slot[1] = down_prod[c].at(out);
+            es.push_back(e);
+        }
+        return es;
+    }
+
+    // Merge identical entries, then repeatedly combine entries that differ
+    // in exactly one mode into one entry whose factor on that mode is a
+    // linear combination (a "combo" slot, evaluated by COMBO ops).
+    std::vector<Proto> combine(std::vector<Proto> es, const std::vector<int>& dims,
+                               std::vector<std::vector<Proto>>& combo_rounds) {
+        int D = (int)dims.size();
+        {
+            std::map<std::pair<int, std::vector<int>>, size_t> seen;
+            std::vector<Proto> out;
+            for (auto& e : es) {
+                auto key = std::make_pair(e.out, e.slot);
+                auto it = seen.find(key);
+                if (it == seen.end()) { seen[key] = out.size(); out.push_back(e); }
+                else out[it->second].w += e.w;
+            }
+            es.swap(out);
+        }
+        for (int round = 0; round < 4 * D; ++round) {
+            int best = -1; size_t best_gain = 0;
+            for (int j = 0; j < D; ++j) {
+                std::map<std::pair<int, std::vector<int>>, size_t> cnt;
+                for (auto& e : es) {
+                    auto s = e.slot; s[j] = -2;
+                    cnt[{e.out, s}]++;
+                }
+                size_t gain = 0;
+                for (auto& kv : cnt) gain += kv.second - 1;
+                if (gain > best_gain) { best_gain = gain; best = j; }
+            }
+            if (best < 0) break;
+            std::map<std::pair<int, std::vector<int>>, std::vector<size_t>> groups;
+            for (size_t i = 0; i < es.size(); ++i) {
+                auto s = es[i].slot; s[best] = -2;
+                groups[{es[i].out, s}].push_back(i);
+            }
+            std::vector<Proto> next, combos;
+            for (auto& kv : groups) {
+                if (kv.second.size() == 1) { next.push_back(es[kv.second[0]]); continue; }
+                int cs = new_slot(dims[best], dims[best]);
+                for (size_t i : kv.second) {
+                    Proto ce; ce.w = es[i].w; ce.out = cs; ce.slot.assign(1, es[i].slot[best]);
+                    combos.push_back(ce);
+                }
+                Proto ne = es[kv.second[0]];
+                ne.w = 1.0; ne.slot[best] = cs;
+                next.push_back(ne);
+            }
+            es.swap(next);
+            combo_rounds.push_back(combos);
+        }
+        return es;
+    }
+
+    // ---- emission -----------------------------------------------------------
+    std::pair<int, int> push_entries(const std::vector<Proto>& es) {
+        int e0 = (int)p.entries.size();
+        std::vector<Proto> sorted = es;
+        std::stable_sort(sorted.begin(), sorted.end(), [](const Proto& a, const Proto& b) { return a.out < b.out; });
+        for (auto& e : sorted) {
+            TtnEntry te{};
+            te.wr = e.w.real(); te.wi = e.w.imag(); te.out = e.out;
+            for (int j = 0; j < TTN_MAXD; ++j) te.slot[j] = j < (int)e.slot.size() ? e.slot[j] : -1;
+            p.entries.push_back(te);
+        }
+        return {e0, (int)sorted.size()};
+    }
+
+    OpSpec tensor_op(int type, int z, int k) {
+        OpSpec s;
+        std::memset(&s.op, 0, sizeof(TtnOp));
+        s.op.type = type;
+        s.op.D = (int)t.dims[z].size();
+        for (int j = 0; j < s.op.D; ++j) s.op.dims[j] = t.dims[z][j];
+        s.op.k = k;
+        s.a_off = p.tensor_off[z];
+        return s;
+    }
+    OpSpec bond_op(int type, int c) {
+        OpSpec s;
+        std::memset(&s.op, 0, sizeof(TtnOp));
+        s.op.type = type;
+        s.op.D = 2;
+        s.op.dims[0] = s.op.dims[1] = t.bond[c];
+        s.a_off = p.bond_off;
+        return s;
+    }
+
+    // cached per-node / per-bond operator entry ranges
+    std::vector<std::vector<std::pair<int, int>>> heff_combo, bond_combo;
+    std::vector<std::pair<int, int>> heff_rng, bond_rng, up_rng;
+    std::vector<std::vector<std::pair<int, int>>> down_rng;
+
+    void prepare_entries() {
+        int n = t.n;
+        heff_combo.assign(n, {}); bond_combo.assign(n, {});
+        heff_rng.assign(n, {0, 0}); bond_rng.assign(n, {0, 0}); up_rng.assign(n, {0, 0});
+        down_rng.assign(n, {});
+        for (int z = 0; z < n; ++z) {
+            std::vector<std::vector<Proto>> rounds;
+            auto es = combine(heff_terms(z), t.dims[z], rounds);
+            for (auto& rd : rounds) heff_combo[z].push_back(push_entries(rd));
+            heff_rng[z] = push_entries(es);
+            if (z > 0) {
+                std::vector<std::vector<Proto>> br;
+                auto bs = combine(bond_terms(z), {t.bond[z], t.bond[z]}, br);
+                for (auto& rd : br) bond_combo[z].push_back(push_entries(rd));
+                bond_rng[z] = push_entries(bs);
+                up_rng[z] = push_entries(up_build(z));
+            }
+            if (!t.leaf(z))
+                for (size_t k = 0; k < t.ch[z].size(); ++k) down_rng[z].push_back(push_entries(down_build(z, (int)k)));
+        }
+    }
+
+    void emit_combos(Program& pr, const std::vector<std::pair<int, int>>& rounds) {
+        for (auto& rg : rounds) {
+            if (rg.second == 0) continue;
+            OpSpec s;
+            std::memset(&s.op, 0, sizeof(TtnOp));
+            s.op.type = TTN_OP_COMBO; s.op.e0 = rg.first; s.op.ne = rg.second;
+            pr.ops.push_back(s);
+        }
+    }
+    void emit_env_up(Program& pr, int c) {
+        if (up_rng[c].second == 0) return;
+        OpSpec s = tensor_op(TTN_OP_ENV, c, (int)t.dims[c].size() - 1);
+        s.op.e0 = up_rng[c].first; s.op.ne = up_rng[c].second;
+        pr.ops.push_back(s);
+    }
+    void emit_env_down(Program& pr, int z, int k) {
+        auto rg = down_rng[z][k];
+        if (rg.second == 0) return;
+        OpSpec s = tensor_op(TTN_OP_ENV, z, k);
+        s.op.e0 = rg.first; s.op.ne = rg.second;
+        pr.ops.push_back(s);
+    }
+    void emit_evolve_node(Program& pr, int z) {
+        emit_combos(pr, heff_combo[z]);
+        OpSpec s = tensor_op(TTN_OP_EVOLVE, z, 0);
+        s.op.e0 = heff_rng[z].first; s.op.ne = heff_rng[z].second;
+        s.op.hermitian = h->hermitian ? 1 : 0;
+        s.op.tau_coef = 0.5;
+        pr.ops.push_back(s);
+    }
+    void emit_evolve_bond(Program& pr, int c) {
+        emit_combos(pr, bond_combo[c]);
+        OpSpec s = bond_op(TTN_OP_EVOLVE, c);
+        s.op.e0 = bond_rng[c].first; s.op.ne = bond_rng[c].second;
+        s.op.hermitian = h->hermitian ? 1 : 0;
+        s.op.tau_coef = -0.5;                    // exp(+i dt/2 K): backward bond step
+        pr.ops.push_back(s);
+    }
+    void emit_qr_down(Program& pr, int z, int k) {
+        OpSpec s = tensor_op(TTN_OP_QR_DOWN, z, k);
+        s.b_off = p.bond_off;
+        pr.ops.push_back(s);
+    }
+    void emit_qr_up(Program& pr, int c) {
+        OpSpec s = tensor_op(TTN_OP_QR_UP, c, (int)t.dims[c].size() - 1);
+        s.b_off = p.bond_off;
+        pr.ops.push_back(s);
+    }
+    void emit_absorb_child(Program& pr, int c) {
+        OpSpec s = tensor_op(TTN_OP_ABSORB_CHILD, c, (int)t.dims[c].size() - 1);
+        s.b_off = p.bond_off;
+        pr.ops.push_back(s);
+    }
+    void emit_absorb_parent(Program& pr, int z, int k) {
+        OpSpec s = tensor_op(TTN_OP_ABSORB_PARENT, z, k);
+        s.b_off = p.bond_off;
+        pr.ops.push_back(s);
+    }
+
+    // Recursive projector-splitting sweeps (paper Sec. II.C): S visits the
+    // children in index order and updates the node last; S* is its adjoint.
+    void emit_S(Program& pr, int z) {
+        for (size_t k = 0; k < t.ch[z].size(); ++k) {
+            int c = t.ch[z][k];
+            emit_qr_down(pr, z, (int)k);
+            emit_absorb_child(pr, c);
+            emit_env_down(pr, z, (int)k);
+            emit_S(pr, c);
+            emit_qr_up(pr, c);
+            emit_env_up(pr, c);
+            emit_evolve_bond(pr, c);
+            emit_absorb_parent(pr, z, (int)k);
+        }
+        emit_evolve_node(pr, z);
+    }
+    void emit_Sstar(Program& pr, int z) {
+        emit_evolve_node(pr, z);
+        for (int k = (int)t.ch[z].size() - 1; k >= 0; --k) {
+            int c = t.ch[z][k];
+            emit_qr_down(pr, z, k);
+            emit_env_down(pr, z, k);
+            emit_evolve_bond(pr, c);
+            emit_absorb_child(pr, c);
+            emit_Sstar(pr, c);
+            emit_qr_up(pr, c);
+            emit_env_up(pr, c);
+            emit_absorb_parent(pr, z, k);
+        }
+    }
+
+    // ---- observables ----------------------------------------------------------
+    void make_observables() {
+        int n = t.n;
+        one_slot = const_slot(1, 1, {cplx(1.0)});
+        // Gram matrices <Psi_i^z|Psi_j^z> along every root-to-leaf path.
+        std::vector<int> gram(n, -1);
+        gram[0] = one_slot;
+        for (int z = 1; z < n; ++z) gram[z] = new_slot(t.bond[z], t.bond[z]);
+        p.rdm_prog.assign(n, {}); p.rdm_slot.assign(n, -1);
+        p.vac_prog.assign(n, {}); p.vac_slot.assign(n, -1);
+        for (int l = 0; l < n; ++l) {
+            if (!t.leaf(l)) continue;
+            std::vector<int> path;
+            for (int u = l; u > 0; u = t.parent[u]) path.push_back(u);
+            std::reverse(path.begin(), path.end());
+            Program& pr = p.rdm_prog[l];
+            for (int c : path) {
+                int z = t.parent[c];
+                int k = (int)(std::find(t.ch[z].begin(), t.ch[z].end(), c) - t.ch[z].begin());
+                Proto e; e.w = 1.0; e.out = gram[c]; e.slot.assign(t.dims[z].size(), -1);
+                e.slot.back() = gram[z];
+                auto rg = push_entries({e});
+                OpSpec s = tensor_op(TTN_OP_ENV, z, k);
+                s.op.e0 = rg.first; s.op.ne = rg.second;
+                pr.ops.push_back(s);
+            }
+            int rs = new_slot(t.phys[l], t.phys[l]);
+            p.rdm_slot[l] = rs;
+            Proto e; e.w = 1.0; e.out = rs; e.slot.assign(2, -1); e.slot[1] = gram[l];
+            auto rg = push_entries({e});
+            OpSpec s = tensor_op(TTN_OP_ENV, l, 0);
+            s.op.e0 = rg.first; s.op.ne = rg.second;
+            pr.ops.push_back(s);
+        }
+        // vacuum projections: bottom-up contraction with basis vector 0 on all
+        // leaves but the kept one.
+        std::vector<int> e0_slot(TTN_MAXCHI + 1, -1);
+        for (int keep = 0; keep < n; ++keep) {
+            if (!t.leaf(keep)) continue;
+            Program& pr = p.vac_prog[keep];
+            std::vector<int> res(n, -1);
+            std::vector<int> on_path(n, 0);
+            for (int u = keep; u >= 0; u = t.parent[u]) { on_path[u] = 1; if (u == 0) break; }
+            std::vector<int> order = t.postorder();
+            for (int z : order) {
+                int rows;  // leading dimension of the result: d_keep on the path, else 1
+                OpSpec s = tensor_op(TTN_OP_CONTRACT_VEC, z, 0);
+                Proto e; e.w = 1.0; e.out = -1; e.slot.assign(t.dims[z].size(), -1);
+                if (t.leaf(z)) {
+                    if (z == keep) {
+                        // the kept leaf's tensor itself is the factor for its parent
+                        rows = t.phys[z];
+                        int sl = new_slot(rows, t.dims[z].back());
+                        e.slot[0] = -1;
+                        res[z] = sl;
+                        auto rg = push_entries({e});
+                        s.op.e0 = rg.first; s.op.ne = rg.second;
+                        s.op.k = sl;                   // output slot
+                        pr.ops.push_back(s);
+                        continue;
+                    }
+                    int d = t.phys[z];
+                    if (e0_slot[d] < 0) {
+                        std::vector<cplx> v(d, 0.0); v[0] = 1.0;
+                        e0_slot[d] = const_slot(1, d, v);
+                    }
+                    e.slot[0] = e0_slot[d];
+                    rows = 1;
+                } else {
+                    rows = 1;
+                    for (size_t k = 0; k < t.ch[z].size(); ++k) {
+                        int c = t.ch[z][k];
+                        e.slot[k] = res[c];
+                        if (on_path[c]) rows = t.phys[keep];
+                    }
+                }
+                int sl = new_slot(rows, t.dims[z].back());
+                res[z] = sl;
+                auto rg = push_entries({e});
+                s.op.e0 = rg.first; s.op.ne = rg.second;
+                s.op.k = sl;
+                pr.ops.push_back(s);
+            }
+            p.vac_slot[keep] = res[0];
+        }
+        // norm and energy at the root
+        {
+            Program& pr = p.norm_energy_prog;
+            OpSpec s = tensor_op(TTN_OP_DOT, 0, 0);
+            s.op.ne = 0;
+            s.out_off = p.scal_off;
+            pr.ops.push_back(s);
+            if (h) {
+                emit_combos(pr, heff_combo[0]);
+                OpSpec e = tensor_op(TTN_OP_DOT, 0, 0);
+                e.op.e0 = heff_rng[0].first; e.op.ne = heff_rng[0].second;
+                e.out_off = p.scal_off + 16;
+                pr.ops.push_back(e);
+            }
+        }
+    }
+};
+
+}  // namespace
+
+std::string make_plan(const Tree& t, const Hamiltonian* h, int precision, Plan& p) {
+    p = Plan();
+    p.esz = precision == 1 ? 8 : 16;   // 1: mixed precision (complex64 bulk)
+    // ---- state arena --------------------------------------------------------
+    int64_t off = 0;
+    p.tensor_off.assign(t.n, 0);
+    int64_t smax = 1;
+    int max_chi = 1;
+    for (int z = 0; z < t.n; ++z) {
+        p.tensor_off[z] = off;
+        off = align_up(off + t.size[z] * (int64_t)p.esz_state, 256);
+        smax = std::max(smax, t.size[z]);
+        for (int d : t.dims[z]) max_chi = std::max(max_chi, d);
+    }
+    smax = std::max<int64_t>(smax, (int64_t)max_chi * max_chi);
+    p.max_chi = max_chi;
+    p.smax = align_up(smax, 32);
+    p.bond_off = off;
+    off = align_up(off + (int64_t)max_chi * max_chi * 16, 256);
+    p.work_off = off;
+    // (KMAX+1) Krylov vectors + 2 scratch tensors in the bulk type, then 2
+    // FP64 QR matrices
+    off = align_up(off + (int64_t)(TTN_KMAX + 3) * p.smax * (int64_t)p.esz + 2 * p.smax * 16, 256);
+    p.status_off = off; off += 64;
+    p.steps_off = off; off += 64;
+    p.scal_off = off; off = align_up(off + 16 * 16, 256);
+    p.max_stamps = 4096;
+    p.stamps_off = off; off = align_up(off + 8 * (int64_t)p.max_stamps, 256);
+    p.total_bytes = off;
+
+    // ---- operators and programs ---------------------------------------------
+    Builder b(t, h, p);
+    b.make_channels();
+    if (h) {
+        b.prepare_entries();
+        for (int z : t.postorder())
+            if (z > 0) b.emit_env_up(p.init_prog, z);
+        b.emit_S(p.step_prog, 0);
+        b.emit_Sstar(p.step_prog, 0);
+        OpSpec s;
+        std::memset(&s.op, 0, sizeof(TtnOp));
+        s.op.type = TTN_OP_STEP_END;
+        p.step_prog.ops.push_back(s);
+    }
+    b.make_observables();
+    // slot storage (complex elements of the bulk type)
+    int64_t soff = 0;
+    for (auto& s : p.slots) {
+        s.off = soff;
+        soff = align_up(soff + (int64_t)s.rows * s.cols * (int64_t)p.esz, 256);
+    }
+    (void)soff;
+    return "";
+}
+
+void product_state(const Tree& t, const std::vector<std::vector<cplx>>& leaf_vecs,
+                   std::vector<std::vector<cplx>>& A) {
+    A.assign(t.n, {});
+    for (int z = 0; z < t.n; ++z) {
+        const auto& dims = t.dims[z];
+        int N = dims.back();
+        int64_t rows = t.size[z] / N;
+        A[z].assign(t.size[z], 0.0);
+        if (t.leaf(z)) {
+            int d = t.phys[z];
+            std::vector<std::vector<cplx>> cols;
+            std::vector<cplx> v = leaf_vecs[z];
+            double nrm = 0;
+            for (auto& x : v) nrm += std::norm(x);
+            nrm = std::sqrt(nrm);
+            for (auto& x : v) x /= nrm;
+            cols.push_back(v);
+            int j = 0;
+            while ((int)cols.size() < N && j < d) {
+                std::vector<cplx> e(d, 0.0);
+                e[j++] = 1.0;
+                for (int pass = 0; pass < 2; ++pass)
+                    for (auto& c : cols) {
+                        cplx h = 0;
+                        for (int i = 0; i < d; ++i) h += std::conj(c[i]) * e[i];
+                        for (int i = 0; i < d; ++i) e[i] -= c[i] * h;
+                    }
+                double en = 0;
+                for (auto& x : e) en += std::norm(x);
+                en = std::sqrt(en);
+                if (en > 0.5) {
+                    for (auto& x : e) x /= en;
+                    cols.push_back(e);
+                }
+            }
+            for (int i = 0; i < d; ++i)
+                for (int c = 0; c < N; ++c) A[z][i * N + c] = cols[c][i];
+        } else {
+            for (int c = 0; c < N && c < rows; ++c) A[z][c * N + c] = 1.0;
+        }
+    }
+}
+
+}  // namespace ttn

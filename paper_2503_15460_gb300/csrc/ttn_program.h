@@ -1,0 +1,78 @@
+// Device program format shared by the host planner (ttn_plan.cpp) and the
+// device interpreter (ttn_kernels.cu).
+//
+// A sweep is compiled on the host into a flat list of operations on one
+// instance's device arena.  Every operand is an absolute device pointer, so
+// the interpreter does no address arithmetic beyond tensor indexing.
+//
+// Operators are "sums of product entries": each entry carries a complex
+// weight and, per tensor index ("mode"), the id of a square matrix slot or
+// -1 for the identity.  The same format expresses
+//   * the effective Hamiltonian of a node  sum_e w_e (x_j M_ej) A  (paper
+//     Eq. psi_eom_1 after term grouping),
+//   * the bond operator  sum_e w_e h_e C H_e^T  (a node with two modes),
+//   * environment builds  out_e += w_e * Q^dag (x_{j != keep} M_ej) Q, and
+//   * linear combinations of matrices (combos).
+#pragma once
+#include <stdint.h>
+
+#define TTN_MAXD 8      // tensor modes per node (children + parent)
+#define TTN_KMAX 32     // maximal Krylov dimension
+#define TTN_MAXCHI 64   // largest bond / local dimension
+
+enum TtnOpType : int {
+    TTN_OP_QR_DOWN = 1,      // A (a) = Q x_k R^T ;  bond buffer (b) <- R^T      (C[n_spf, m_shf])
+    TTN_OP_QR_UP = 2,        // A (a) = Q x_last R;  bond buffer (b) <- R
+    TTN_OP_ABSORB_CHILD = 3, // A (a) <- A x_last B^T   with B = bond buffer (b)
+    TTN_OP_ABSORB_PARENT = 4,// A (a) <- B x_k A
+    TTN_OP_ENV = 5,          // out slots of entries += w * Q^dag (x_{j!=k} M_j) Q   (Q = a, keep mode k)
+    TTN_OP_COMBO = 6,        // out slot of entries = sum w * M (slot[0] = -1: identity)
+    TTN_OP_EVOLVE = 7,       // a <- exp(-i tau H) a, tau = tau_coef * dt, H = entries
+    TTN_OP_DOT = 8,          // out scalar <- <a, H a> (ne > 0) or <a, a> (ne == 0)
+    TTN_OP_TRACE = 9,        // out scalar <- sum_ab slot0[a,b] * slot1[b,a]   (k = dim)
+    TTN_OP_CONTRACT_VEC = 10,// a' <- contraction of tensor a with matrices on modes (vacuum projection)
+    TTN_OP_STEP_END = 11     // end of one time step (timestamp, step counter)
+};
+
+struct TtnEntry {
+    double wr, wi;          // complex weight
+    int out;                // output slot (ENV, COMBO) or -1
+    int slot[TTN_MAXD];     // factor slot per mode, -1 = identity
+};
+
+struct TtnSlot {
+    void* ptr;              // device pointer to a dim x dim row-major complex matrix
+                            // (rows x cols for CONTRACT_VEC factors)
+    int rows, cols;
+};
+
+struct TtnOp {
+    int type;
+    int D;                  // number of modes of tensor a
+    int dims[TTN_MAXD];     // mode dimensions of tensor a
+    int k;                  // mode argument
+    int e0, ne;             // entry range
+    int hermitian;          // EVOLVE: Lanczos (1) or Arnoldi (0)
+    int pad;
+    double tau_coef;        // EVOLVE
+    void* a;                // main operand
+    void* b;                // bond buffer / second operand / output tensor
+    double* out;            // DOT / TRACE: complex scalar output (2 doubles)
+};
+
+struct TtnInstance {
+    const TtnOp* ops;
+    int n_ops;              // ops of one time step (or of one observable program)
+    int n_slots;
+    const TtnEntry* entries;
+    const TtnSlot* slots;
+    void* work;             // workspace: (KMAX+1) Krylov vectors + 4 scratch tensors
+    int64_t smax;           // length (complex elements) of each workspace vector
+    int* status;            // device status word (0 = ok, else ttn_status code)
+    int* steps_done;        // device step counter
+    unsigned long long* stamps;  // optional per-step completion time stamps (ns)
+    double ktol;
+    double qtol;            // QR rank threshold relative to ||M||_F
+    int kmax;
+    int pad;
+};

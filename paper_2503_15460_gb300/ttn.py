@@ -1,0 +1,255 @@
+"""Python binding of libttn (include/ttn.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls and converts
+NumPy arrays to the C layouts; all computation happens in the CUDA library.
+If ``libttn.so`` has not been built this module raises on import -- there is
+no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libttn.so")
+
+TTN_OK, TTN_E_INVALID, TTN_E_OOM, TTN_E_CUDA, TTN_E_NOCONV, TTN_E_TIMEOUT, TTN_E_STATE = range(7)
+TTN_FP64, TTN_MIXED = 0, 1
+STATUS_NAMES = {0: "TTN_OK", 1: "TTN_E_INVALID", 2: "TTN_E_OOM", 3: "TTN_E_CUDA",
+                4: "TTN_E_NOCONV", 5: "TTN_E_TIMEOUT", 6: "TTN_E_STATE"}
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with paper_2503_15460_gb300.build.build()")
+_lib = C.CDLL(LIB_PATH)
+
+
+class ttn_step_opts(C.Structure):
+    _fields_ = [("krylov_tol", C.c_double), ("krylov_maxdim", C.c_int),
+                ("eps_spawn", C.c_double), ("chi_max", C.c_int), ("expand", C.c_int),
+                ("qr_rank_tol", C.c_double)]
+
+
+_P = C.c_void_p
+_I32 = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+_I64 = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
+_C128 = np.ctypeslib.ndpointer(dtype=np.complex128, flags="C_CONTIGUOUS")
+_F64 = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+
+_sig = {
+    "ttn_create": ([C.c_int, _I32, _I32, _I32, C.c_int, C.POINTER(_P)], C.c_int),
+    "ttn_set_state": ([_P, _C128, _I64], C.c_int),
+    "ttn_set_product_state": ([_P, _C128, _I64], C.c_int),
+    "ttn_set_sop_hamiltonian": ([_P, C.c_int, _C128, _I32, _I32, _C128, _I64, C.c_int], C.c_int),
+    "ttn_step": ([_P, C.c_double, C.c_int, C.POINTER(ttn_step_opts)], C.c_int),
+    "ttn_step_batch": ([C.POINTER(_P), C.c_int, C.c_double, C.c_int, C.POINTER(ttn_step_opts)], C.c_int),
+    "ttn_reduced_density": ([_P, C.c_int, _C128], C.c_int),
+    "ttn_expect": ([_P, C.c_int, _I32, _C128, _I64, _C128], C.c_int),
+    "ttn_norm_energy": ([_P, C.POINTER(C.c_double), _C128], C.c_int),
+    "ttn_vacuum_projection": ([_P, C.c_int, _C128], C.c_int),
+    "ttn_get_state": ([_P, _C128, _I64], C.c_int),
+    "ttn_bond_dims": ([_P, _I32], C.c_int),
+    "ttn_set_stream": ([_P, _P], C.c_int),
+    "ttn_device_bytes": ([_P, C.POINTER(C.c_size_t)], C.c_int),
+    "ttn_last_error": ([_P], C.c_char_p),
+    "ttn_destroy": ([_P], None),
+}
+for _name, (_args, _res) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+EXPORTED = tuple(_sig)
+
+
+class TTNError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(st, ctx):
+    if st != TTN_OK:
+        raise TTNError(st, ttn_last_error(ctx))
+
+
+def ttn_last_error(ctx) -> str:
+    m = _lib.ttn_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def ttn_create(parent, phys_dim, bond_dim, precision=TTN_FP64):
+    parent = np.ascontiguousarray(parent, dtype=np.int32)
+    phys = np.ascontiguousarray(phys_dim, dtype=np.int32)
+    bond = np.ascontiguousarray(bond_dim, dtype=np.int32)
+    h = _P()
+    st = _lib.ttn_create(len(parent), parent, phys, bond, int(precision), C.byref(h))
+    _check(st, None)
+    return h
+
+
+def _flatten(tensors):
+    offs = np.zeros(len(tensors) + 1, dtype=np.int64)
+    for i, a in enumerate(tensors):
+        offs[i + 1] = offs[i] + np.asarray(a).size
+    flat = np.ascontiguousarray(np.concatenate([np.asarray(a, dtype=np.complex128).ravel() for a in tensors]))
+    return flat, offs
+
+
+def ttn_set_state(ctx, tensors):
+    flat, offs = _flatten(tensors)
+    _check(_lib.ttn_set_state(ctx, flat, offs), ctx)
+
+
+def ttn_set_product_state(ctx, leaf_vecs: dict, n_nodes: int):
+    vecs, offs, o = [], np.zeros(n_nodes, dtype=np.int64), 0
+    for z in range(n_nodes):
+        offs[z] = o
+        if z in leaf_vecs:
+            v = np.asarray(leaf_vecs[z], dtype=np.complex128).ravel()
+            vecs.append(v); o += v.size
+    flat = np.ascontiguousarray(np.concatenate(vecs)) if vecs else np.zeros(1, np.complex128)
+    _check(_lib.ttn_set_product_state(ctx, flat, offs), ctx)
+
+
+def ttn_set_sop_hamiltonian(ctx, coeff, term_ptr, factor_leaf, factor_mats, factor_mat_off, hermitian):
+    coeff = np.ascontiguousarray(coeff, dtype=np.complex128)
+    term_ptr = np.ascontiguousarray(term_ptr, dtype=np.int32)
+    factor_leaf = np.ascontiguousarray(factor_leaf, dtype=np.int32)
+    if factor_leaf.size == 0:
+        factor_leaf = np.zeros(1, np.int32)
+    mats = np.ascontiguousarray(factor_mats, dtype=np.complex128)
+    if mats.size == 0:
+        mats = np.zeros(1, np.complex128)
+    off = np.ascontiguousarray(factor_mat_off, dtype=np.int64)
+    if off.size == 0:
+        off = np.zeros(1, np.int64)
+    _check(_lib.ttn_set_sop_hamiltonian(ctx, len(coeff), coeff, term_ptr, factor_leaf, mats, off,
+                                        int(bool(hermitian))), ctx)
+
+
+def _opts(opts):
+    if opts is None:
+        return None
+    if isinstance(opts, ttn_step_opts):
+        return C.byref(opts)
+    o = ttn_step_opts(**opts)
+    return C.byref(o)
+
+
+def ttn_step(ctx, dt, nsteps=1, opts=None):
+    _check(_lib.ttn_step(ctx, float(dt), int(nsteps), _opts(opts)), ctx)
+
+
+def ttn_step_batch(ctxs, dt, nsteps=1, opts=None):
+    arr = (_P * len(ctxs))(*[c.value if isinstance(c, _P) else c for c in ctxs])
+    st = _lib.ttn_step_batch(arr, len(ctxs), float(dt), int(nsteps), _opts(opts))
+    if st != TTN_OK:
+        msgs = "; ".join(ttn_last_error(c) for c in ctxs if ttn_last_error(c))
+        raise TTNError(st, msgs)
+
+
+def ttn_reduced_density(ctx, leaf, d):
+    out = np.zeros(d * d, dtype=np.complex128)
+    _check(_lib.ttn_reduced_density(ctx, int(leaf), out), ctx)
+    return out.reshape(d, d)
+
+
+def ttn_expect(ctx, leaves, ops):
+    leaves = np.ascontiguousarray(leaves, dtype=np.int32)
+    flat, offs = _flatten(ops)
+    out = np.zeros(len(leaves), dtype=np.complex128)
+    _check(_lib.ttn_expect(ctx, len(leaves), leaves, flat, offs[:-1].copy(), out), ctx)
+    return out
+
+
+def ttn_norm_energy(ctx):
+    n = C.c_double(0.0)
+    e = np.zeros(1, dtype=np.complex128)
+    _check(_lib.ttn_norm_energy(ctx, C.byref(n), e), ctx)
+    return n.value, complex(e[0])
+
+
+def ttn_vacuum_projection(ctx, keep_leaf, d):
+    out = np.zeros(d, dtype=np.complex128)
+    _check(_lib.ttn_vacuum_projection(ctx, int(keep_leaf), out), ctx)
+    return out
+
+
+def ttn_get_state(ctx, sizes):
+    total = int(np.sum(sizes))
+    flat = np.zeros(total, dtype=np.complex128)
+    offs = np.zeros(len(sizes) + 1, dtype=np.int64)
+    _check(_lib.ttn_get_state(ctx, flat, offs), ctx)
+    return [flat[offs[i]:offs[i + 1]] for i in range(len(sizes))]
+
+
+def ttn_bond_dims(ctx, n_nodes):
+    out = np.zeros(n_nodes, dtype=np.int32)
+    _check(_lib.ttn_bond_dims(ctx, out), ctx)
+    return out
+
+
+def ttn_set_stream(ctx, stream_handle: int):
+    _check(_lib.ttn_set_stream(ctx, C.c_void_p(int(stream_handle))), ctx)
+
+
+def ttn_device_bytes(ctx):
+    n = C.c_size_t(0)
+    _check(_lib.ttn_device_bytes(ctx, C.byref(n)), ctx)
+    return n.value
+
+
+def ttn_destroy(ctx):
+    _lib.ttn_destroy(ctx)
+
+
+# ---------------------------------------------------------------------------
+# convenience wrapper around a context handle
+# ---------------------------------------------------------------------------
+class Context:
+    """Owns one ttn_ctx.  ``tree`` is a workloads.Tree (parent/phys_dim/bond_dim)."""
+
+    def __init__(self, tree, precision=TTN_FP64):
+        self.tree = tree
+        self.precision = precision
+        self.h = ttn_create(tree.parent, tree.phys_dim, tree.bond_dim, precision)
+
+    def set_state(self, tensors):
+        ttn_set_state(self.h, tensors)
+
+    def set_hamiltonian(self, H):
+        coeff, term_ptr, leaf, mats, off = H.to_csr()
+        ttn_set_sop_hamiltonian(self.h, coeff, term_ptr, leaf, mats, off, H.hermitian)
+
+    def step(self, dt, nsteps=1, opts=None):
+        ttn_step(self.h, dt, nsteps, opts)
+
+    def rdm(self, leaf):
+        return ttn_reduced_density(self.h, leaf, int(self.tree.phys_dim[leaf]))
+
+    def populations(self, leaves):
+        return [np.real(np.diag(self.rdm(l))) for l in leaves]
+
+    def norm_energy(self):
+        return ttn_norm_energy(self.h)
+
+    def vacuum_projection(self, keep_leaf):
+        return ttn_vacuum_projection(self.h, keep_leaf, int(self.tree.phys_dim[keep_leaf]))
+
+    def get_state(self):
+        sizes = [int(np.prod(self.tree.mode_dims(z))) for z in range(self.tree.n)]
+        flat = ttn_get_state(self.h, sizes)
+        return [f.reshape(self.tree.mode_dims(z)) for z, f in enumerate(flat)]
+
+    def close(self):
+        if self.h:
+            ttn_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
