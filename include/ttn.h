@@ -65,7 +65,7 @@ enum { TTN_FP64 = 0, TTN_MIXED = 1 };
 typedef struct {
     double krylov_tol;   /* stop when Saad's a-posteriori error estimate of the
                             projected exponential is below krylov_tol * ||v||;
-                            <= 0 selects 1e-13 (FP64) or 1e-8 (MIXED)            */
+                            <= 0 selects 1e-13 (FP64) or 1e-10 (MIXED)           */
     int krylov_maxdim;   /* Krylov dimension before the interval is halved,
                             1..32; <= 0 selects 32                               */
     double eps_spawn;    /* subspace-expansion tolerance (Sec. II.D); unused
@@ -76,7 +76,7 @@ typedef struct {
     double qr_rank_tol;  /* a QR column whose remainder has norm <= qr_rank_tol
                             * ||M||_F is treated as zero and completed by the
                             deterministic unit vector (unoccupied function);
-                            <= 0 selects 1e-10 (FP64) or 1e-8 (MIXED)            */
+                            <= 0 selects 1e-10 (both modes)                      */
 } ttn_step_opts;
 
 /* Create a context for a tree (Sec. II.A).
@@ -173,6 +173,28 @@ ttn_status ttn_get_state(ttn_ctx* ctx, ttn_c128* tensors, int64_t* offsets);
 
 /* Bond dimension of every node to its parent (root: 1), out[n_nodes]. */
 ttn_status ttn_bond_dims(ttn_ctx* ctx, int* out);
+
+/* Make `device` the CUDA device on which the calling thread's subsequent
+ * ttn_create calls allocate (the library carries its own CUDA runtime, so
+ * a device selected through another runtime, e.g. PyTorch's, is not seen). */
+ttn_status ttn_set_device(int device);
+
+/* Step statistics of a context: total steps done since creation, the
+ * algorithmic floating-point operations executed by its device programs
+ * (complex multiply-add = 8; effective-Hamiltonian mode products, Gram-
+ * Schmidt, environment builds, QR and bond absorption), and the device
+ * completion time stamps (globaltimer, ns) of the last min(max_stamps,
+ * steps, 4096) steps, oldest first.  Any output pointer may be NULL. */
+ttn_status ttn_step_stats(ttn_ctx* ctx, int64_t* steps_done, double* flops, uint64_t* stamps,
+                          int max_stamps, int* n_stamps);
+
+/* SM clock cycles the context's device programs spent per operation type,
+ * cycles[32] (index: 1 QR towards a child, 2 QR towards the parent,
+ * 3/4 bond absorption into child/parent, 5 environment builds, 6 operator
+ * combinations, 7 Krylov exponentials, 8-10 observables, 11 step end;
+ * inside those: 16 effective-Hamiltonian products, 17 Gram-Schmidt,
+ * 18 small projected exponentials, 19 Gram contractions, 20 conversions). */
+ttn_status ttn_op_cycles(ttn_ctx* ctx, uint64_t* cycles);
 
 /* Run all further work of the context on this cudaStream_t. */
 ttn_status ttn_set_stream(ttn_ctx* ctx, void* cuda_stream);

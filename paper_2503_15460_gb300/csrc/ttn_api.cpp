@@ -104,8 +104,10 @@ TtnInstance make_instance(ttn_ctx* c, const DevProgram& p) {
     in.status = (int*)(c->d_state + c->plan.status_off);
     in.steps_done = (int*)(c->d_state + c->plan.steps_off);
     in.stamps = (unsigned long long*)(c->d_state + c->plan.stamps_off);
-    in.ktol = c->ktol > 0 ? c->ktol : (c->precision == TTN_MIXED ? 1e-8 : 1e-13);
-    in.qtol = c->qtol > 0 ? c->qtol : (c->precision == TTN_MIXED ? 1e-8 : 1e-10);
+    in.flops = (double*)(c->d_state + c->plan.flops_off);
+    in.op_cycles = (unsigned long long*)(c->d_state + c->plan.cycles_off);
+    in.ktol = c->ktol > 0 ? c->ktol : (c->precision == TTN_MIXED ? 1e-10 : 1e-13);
+    in.qtol = c->qtol > 0 ? c->qtol : 1e-10;
     in.kmax = c->kmax;
     return in;
 }
@@ -460,6 +462,44 @@ ttn_status ttn_get_state(ttn_ctx* c, ttn_c128* tensors, int64_t* offsets) {
 ttn_status ttn_bond_dims(ttn_ctx* c, int* out) {
     if (!c || !out) return TTN_E_INVALID;
     for (int z = 0; z < c->tree.n; ++z) out[z] = z == 0 ? 1 : c->tree.bond[z];
+    return TTN_OK;
+}
+
+ttn_status ttn_set_device(int device) {
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) return fail(nullptr, TTN_E_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+    return TTN_OK;
+}
+
+ttn_status ttn_step_stats(ttn_ctx* c, int64_t* steps_done, double* flops, uint64_t* stamps, int max_stamps,
+                          int* n_stamps) {
+    if (!c) return TTN_E_INVALID;
+    cudaSetDevice(c->device);
+    int steps = 0;
+    double fl = 0.0;
+    CK(cudaMemcpyAsync(&steps, c->d_state + c->plan.steps_off, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "stats copy");
+    CK(cudaMemcpyAsync(&fl, c->d_state + c->plan.flops_off, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "stats copy");
+    std::vector<unsigned long long> raw(c->plan.max_stamps);
+    CK(cudaMemcpyAsync(raw.data(), c->d_state + c->plan.stamps_off, raw.size() * 8, cudaMemcpyDeviceToHost, c->stream), "stats copy");
+    CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+    if (steps_done) *steps_done = steps;
+    if (flops) *flops = fl;
+    int n = std::min(std::min(max_stamps, steps), c->plan.max_stamps);
+    if (n < 0) n = 0;
+    if (stamps)
+        for (int i = 0; i < n; ++i) {
+            int s = steps - n + i;
+            stamps[i] = raw[s % c->plan.max_stamps];
+        }
+    if (n_stamps) *n_stamps = stamps ? n : 0;
+    return TTN_OK;
+}
+
+ttn_status ttn_op_cycles(ttn_ctx* c, uint64_t* cycles) {
+    if (!c || !cycles) return TTN_E_INVALID;
+    cudaSetDevice(c->device);
+    CK(cudaMemcpyAsync(cycles, c->d_state + c->plan.cycles_off, 32 * 8, cudaMemcpyDeviceToHost, c->stream), "cycles copy");
+    CK(cudaStreamSynchronize(c->stream), "stream synchronize");
     return TTN_OK;
 }
 

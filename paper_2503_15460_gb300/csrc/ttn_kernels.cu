@@ -21,6 +21,22 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 
+// Algorithmic floating-point operations of this block (complex multiply-add
+// = 8), accumulated by thread 0 and flushed to the instance counter at exit.
+__shared__ double s_flops;
+__device__ __forceinline__ void count_flops(double f) { if (threadIdx.x == 0) s_flops += f; }
+
+// Sub-phase cycle counters (thread 0), flushed with the op counters.
+__shared__ unsigned long long s_sub[8];
+__device__ __forceinline__ long long sub_start() { return clock64(); }
+__device__ __forceinline__ void sub_stop(int idx, long long t0) {
+    if (threadIdx.x == 0) s_sub[idx] += (unsigned long long)(clock64() - t0);
+}
+
+// Dynamic shared memory: a staging area for operator matrices and tiles.
+constexpr int kStageBytes = 64 * 1024;
+extern __shared__ __align__(16) unsigned char dyn_smem[];
+
 // ---------------------------------------------------------------------------
 // complex helpers
 // ---------------------------------------------------------------------------
@@ -54,6 +70,15 @@ __device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
     acc.x = fmaf(a.x, b.x, acc.x); acc.x = fmaf(-a.y, b.y, acc.x);
     acc.y = fmaf(a.x, b.y, acc.y); acc.y = fmaf(a.y, b.x, acc.y);
 }
+// acc += conj(a) * b in the element type's precision
+__device__ __forceinline__ void cfmaconj(double2& acc, double2 a, double2 b) {
+    acc.x = fma(a.x, b.x, acc.x); acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y); acc.y = fma(-a.y, b.x, acc.y);
+}
+__device__ __forceinline__ void cfmaconj(float2& acc, float2 a, float2 b) {
+    acc.x = fmaf(a.x, b.x, acc.x); acc.x = fmaf(a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y); acc.y = fmaf(-a.y, b.x, acc.y);
+}
 template <class T> __device__ __forceinline__ T czero();
 template <> __device__ __forceinline__ double2 czero<double2>() { return make_double2(0.0, 0.0); }
 template <> __device__ __forceinline__ float2 czero<float2>() { return make_float2(0.f, 0.f); }
@@ -78,7 +103,7 @@ struct Smem {
     double2 y[TTN_KMAX + 1];
     double2 u[TTN_KMAX + 1];
     double2 dots[TTN_KMAX + 1];
-    double2 red[kWarps];
+    double2 red[kWarps * 4];
     double2 bc[4];
     double2 qtau[TTN_MAXCHI];
     int qskip[TTN_MAXCHI];
@@ -102,11 +127,32 @@ __device__ double2 block_sum(double2 v, Smem& sm) {
     return r;
 }
 
+// Four block-wide sums at once (one barrier round); results in sm.bc[0..3].
+__device__ void block_sum4(double2 v[4], Smem& sm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        v[q] = warp_sum(v[q]);
+        if (lane == 0) sm.red[warp * 4 + q] = v[q];
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            double2 w = lane < kWarps ? sm.red[lane * 4 + q] : make_double2(0.0, 0.0);
+            w = warp_sum(w);
+            if (lane == 0) sm.bc[q] = w;
+        }
+    }
+    __syncthreads();
+}
+
 template <class T>
 __device__ double2 block_dot(const T* __restrict__ a, const T* __restrict__ b, int64_t n, Smem& sm) {
-    double2 acc = make_double2(0.0, 0.0);
-    for (int64_t i = threadIdx.x; i < n; i += kThreads) acc = cadd(acc, cconjmul(cd(a[i]), cd(b[i])));
-    return block_sum(acc, sm);
+    T acc = czero<T>();
+    for (int64_t i = threadIdx.x; i < n; i += kThreads) cfmaconj(acc, a[i], b[i]);
+    count_flops(8.0 * n);
+    return block_sum(cd(acc), sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -121,10 +167,11 @@ struct Shape {
 };
 
 // out[l, p, r] (+)= w * sum_m M[p, m] in[l, m, r]   (M: nout x nin, or its
-// transpose stored nin x nout when transM)
+// transpose stored nin x nout when transM).  Generic version: one output
+// per thread.
 template <class T>
-__device__ void mode_prod(T* __restrict__ out, const T* __restrict__ in, int64_t L, int nin, int nout,
-                          int64_t R, const T* __restrict__ M, bool transM, double2 w, bool accumulate) {
+__device__ void mode_prod_simple(T* __restrict__ out, const T* __restrict__ in, int64_t L, int nin, int nout,
+                                 int64_t R, const T* __restrict__ M, bool transM, double2 w, bool accumulate) {
     const int64_t total = L * nout * R;
     const T wt = cT<T>(w);
     for (int64_t idx = threadIdx.x; idx < total; idx += kThreads) {
@@ -145,6 +192,56 @@ __device__ void mode_prod(T* __restrict__ out, const T* __restrict__ in, int64_t
         if (accumulate) { T o = out[idx]; o.x += v.x; o.y += v.y; out[idx] = o; }
         else out[idx] = v;
     }
+}
+
+// Square mode product with the matrix staged in shared memory and each
+// fibre in[l, :, r] held in registers: every thread produces all n outputs
+// of its fibre, reading the matrix rows as shared-memory broadcasts.
+template <class T, int MAXN>
+__device__ void mode_prod_tiled(T* __restrict__ out, const T* __restrict__ in, int64_t L, int n, int64_t R,
+                                const T* __restrict__ M, double2 w, bool accumulate) {
+    T* Ms = (T*)dyn_smem;
+    for (int i = threadIdx.x; i < n * n; i += kThreads) Ms[i] = M[i];
+    __syncthreads();
+    const int64_t F = L * R;
+    const T wt = cT<T>(w);
+    for (int64_t f = threadIdx.x; f < F; f += kThreads) {
+        const int64_t l = f / R, r = f - (f / R) * R;
+        const T* src = in + l * n * R + r;
+        T* dst = out + l * n * R + r;
+        T x[MAXN];
+#pragma unroll
+        for (int m = 0; m < MAXN; ++m) x[m] = (m < n) ? src[m * R] : czero<T>();
+        for (int p = 0; p < n; ++p) {
+            const T* row = Ms + p * n;
+            T acc = czero<T>();
+#pragma unroll
+            for (int m = 0; m < MAXN; ++m)
+                if (m < n) cfma(acc, row[m], x[m]);
+            T v = czero<T>();
+            cfma(v, wt, acc);
+            if (accumulate) { T o = dst[p * R]; o.x += v.x; o.y += v.y; dst[p * R] = o; }
+            else dst[p * R] = v;
+        }
+    }
+    __syncthreads();
+}
+
+template <class T>
+__device__ void mode_prod(T* __restrict__ out, const T* __restrict__ in, int64_t L, int nin, int nout,
+                          int64_t R, const T* __restrict__ M, bool transM, double2 w, bool accumulate) {
+    count_flops(8.0 * (double)(L * nout * R) * nin);
+    if (transM || nin != nout || nin > 32) {
+        mode_prod_simple(out, in, L, nin, nout, R, M, transM, w, accumulate);
+        return;
+    }
+    if (nin <= 2) mode_prod_tiled<T, 2>(out, in, L, nin, R, M, w, accumulate);
+    else if (nin <= 4) mode_prod_tiled<T, 4>(out, in, L, nin, R, M, w, accumulate);
+    else if (nin <= 8) mode_prod_tiled<T, 8>(out, in, L, nin, R, M, w, accumulate);
+    else if (nin <= 12) mode_prod_tiled<T, 12>(out, in, L, nin, R, M, w, accumulate);
+    else if (nin <= 16) mode_prod_tiled<T, 16>(out, in, L, nin, R, M, w, accumulate);
+    else if (nin <= 24) mode_prod_tiled<T, 24>(out, in, L, nin, R, M, w, accumulate);
+    else mode_prod_tiled<T, 32>(out, in, L, nin, R, M, w, accumulate);
 }
 
 template <class T>
@@ -207,24 +304,92 @@ __device__ void heff_apply(T* __restrict__ out, const T* __restrict__ in, T* t1,
 }
 
 // G[a, b] += w * sum_{other indices} conj(X[.., a, ..]) Y[.., b, ..]   (index k kept)
+// Tiles of X and Y (all chi values of the kept index for OT positions of
+// the others) are staged in shared memory; every thread accumulates a 2x2
+// block of G, small G are split over groups of positions, and the group
+// partials are reduced in a fixed order (deterministic).
 template <class T>
 __device__ void gram_acc(T* G, const T* __restrict__ X, const T* __restrict__ Y, const Shape& sh, int k, double2 w) {
     const int chi = sh.d[k];
     const int64_t L = sh.before(k), R = sh.after(k), O = L * R;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int pr = warp; pr < chi * chi; pr += kWarps) {
-        const int a = pr / chi, b = pr % chi;
-        double2 acc = make_double2(0.0, 0.0);
-        for (int64_t o = lane; o < O; o += 32) {
-            const int64_t l = o / R, r = o % R;
-            acc = cadd(acc, cconjmul(cd(X[(l * chi + a) * R + r]), cd(Y[(l * chi + b) * R + r])));
+    count_flops(8.0 * (double)O * chi * chi);
+    int OT = (kStageBytes / 2) / (chi * (int)sizeof(T));
+    if (OT > 128) OT = 128;
+    T* Xs = (T*)dyn_smem;            // [OT][chi]
+    T* Ys = Xs + OT * chi;
+    const int tn = (chi + 1) / 2, ntile = tn * tn;
+    int groups = kThreads / ntile;
+    if (groups < 1) groups = 1;
+    if (groups > 8) groups = 8;
+    const int tid = threadIdx.x;
+    const bool active = tid < ntile * groups || ntile > kThreads;
+    T acc[4][2][2];
+    const int nrep = (ntile + kThreads - 1) / kThreads;      // tiles per thread when chi > 32
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) acc[q][i][j] = czero<T>();
+    const int g = (ntile >= kThreads) ? 0 : tid / ntile;
+    const int gcount = (ntile >= kThreads) ? 1 : groups;
+    for (int64_t o0 = 0; o0 < O; o0 += OT) {
+        const int nt = (int)((O - o0) < OT ? (O - o0) : OT);
+        if (R == 1) {
+            const T* xs = X + o0 * chi;
+            const T* ys = Y + o0 * chi;
+            for (int i = tid; i < nt * chi; i += kThreads) { Xs[i] = xs[i]; Ys[i] = ys[i]; }
+        } else {
+            for (int i = tid; i < nt * chi; i += kThreads) {
+                const int oo = i % nt, a = i / nt;
+                const int64_t o = o0 + oo, l = o / R, r = o - (o / R) * R;
+                const int64_t src = (l * chi + a) * R + r;
+                Xs[oo * chi + a] = X[src];
+                Ys[oo * chi + a] = Y[src];
+            }
         }
-        acc = warp_sum(acc);
-        if (lane == 0) {
-            double2 g = cd(G[a * chi + b]);
-            G[a * chi + b] = cT<T>(cadd(g, cmul(w, acc)));
+        __syncthreads();
+        if (active) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (q >= nrep) break;
+                const int tile = (ntile >= kThreads) ? tid + q * kThreads : tid % ntile;
+                if (tile >= ntile) break;
+                const int a0 = 2 * (tile / tn), b0 = 2 * (tile % tn);
+                const bool a1ok = a0 + 1 < chi, b1ok = b0 + 1 < chi;
+                for (int oo = g; oo < nt; oo += gcount) {
+                    const T x0 = Xs[oo * chi + a0];
+                    const T x1 = a1ok ? Xs[oo * chi + a0 + 1] : czero<T>();
+                    const T y0 = Ys[oo * chi + b0];
+                    const T y1 = b1ok ? Ys[oo * chi + b0 + 1] : czero<T>();
+                    cfmaconj(acc[q][0][0], x0, y0); cfmaconj(acc[q][0][1], x0, y1);
+                    cfmaconj(acc[q][1][0], x1, y0); cfmaconj(acc[q][1][1], x1, y1);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // write partials P[g][a][b] and reduce over g in order
+    T* Pp = (T*)dyn_smem;
+    if (active) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (q >= nrep) break;
+            const int tile = (ntile >= kThreads) ? tid + q * kThreads : tid % ntile;
+            if (tile >= ntile) break;
+            const int a0 = 2 * (tile / tn), b0 = 2 * (tile % tn);
+            for (int i = 0; i < 2; ++i)
+                for (int j = 0; j < 2; ++j)
+                    if (a0 + i < chi && b0 + j < chi) Pp[((int64_t)g * chi + a0 + i) * chi + b0 + j] = acc[q][i][j];
         }
     }
+    __syncthreads();
+    for (int ab = tid; ab < chi * chi; ab += kThreads) {
+        double2 sum = make_double2(0.0, 0.0);
+        for (int gg = 0; gg < gcount; ++gg) sum = cadd(sum, cd(Pp[(int64_t)gg * chi * chi + ab]));
+        G[ab] = cT<T>(cadd(cd(G[ab]), cmul(w, sum)));
+    }
+    __syncthreads();
 }
 
 // Environment build: for every entry, out += w * Q^dag (x_{j != keep} M_j) Q.
@@ -242,7 +407,9 @@ __device__ void env_build(const T* Q, T* t1, T* t2, const Shape& sh, int keep, c
             prev = e.out;
         }
         const T* Y = apply_chain(Q, t1, t2, sh, e, slots, keep, (T*)nullptr, make_double2(1.0, 0.0));
+        const long long tg = sub_start();
         gram_acc(out, Q, Y, sh, keep, make_double2(e.wr, e.wi));
+        sub_stop(3, tg);
         __syncthreads();
     }
 }
@@ -310,6 +477,7 @@ __device__ void qr_mode(T* A, const Shape& sh, int k, double2* Wc, double2* Qc, 
         __syncthreads();
         if (threadIdx.x == 0) { x[j] = make_double2(beta, 0.0); sm.qskip[j] = 0; sm.qtau[j] = tau; }
         const double2 ctau = make_double2(tau.x, -tau.y);
+        count_flops(16.0 * (double)(m - j) * (n - j - 1) + 8.0 * (m - j));
         for (int c = j + 1 + warp; c < n; c += kWarps) {
             double2* y = Wc + (int64_t)c * m;
             double2 acc = make_double2(0.0, 0.0);
@@ -336,6 +504,7 @@ __device__ void qr_mode(T* A, const Shape& sh, int k, double2* Wc, double2* Qc, 
         if (sm.qskip[j]) continue;
         const double2 tau = sm.qtau[j];
         const double2* x = Wc + (int64_t)j * m;
+        count_flops(16.0 * (double)(m - j) * (n - j));
         for (int c = j + warp; c < n; c += kWarps) {
             double2* y = Qc + (int64_t)c * m;
             double2 acc = make_double2(0.0, 0.0);
@@ -448,17 +617,37 @@ __device__ int krylov_once(TS* x, const Shape& sh, const TtnEntry* es, int ne, c
     for (int j = 0; j < kmax; ++j) {
         TB* vj = V + (int64_t)j * smax;
         TB* w = V + (int64_t)(j + 1) * smax;
+        const long long th = sub_start();
         heff_apply(w, vj, t1, t2, sh, es, ne, slots);
+        sub_stop(0, th);
+        const long long tgs = sub_start();
         for (int pass = 0; pass < 2; ++pass) {
-            for (int i = 0; i <= j; ++i) {
-                double2 h = block_dot(V + (int64_t)i * smax, w, S, sm);
-                if (threadIdx.x == 0) { sm.dots[i] = h; sm.H[i * TTN_KMAX + j] = cadd(sm.H[i * TTN_KMAX + j], h); }
+            for (int i0 = 0; i0 <= j; i0 += 4) {
+                const int nb = (j + 1 - i0) < 4 ? (j + 1 - i0) : 4;
+                TB acc[4] = {czero<TB>(), czero<TB>(), czero<TB>(), czero<TB>()};
+                for (int64_t e = threadIdx.x; e < S; e += kThreads) {
+                    const TB we = w[e];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (q < nb) cfmaconj(acc[q], V[(int64_t)(i0 + q) * smax + e], we);
+                }
+                double2 d[4] = {cd(acc[0]), cd(acc[1]), cd(acc[2]), cd(acc[3])};
+                block_sum4(d, sm);
+                if (threadIdx.x == 0)
+                    for (int q = 0; q < nb; ++q) {
+                        sm.dots[i0 + q] = sm.bc[q];
+                        sm.H[(i0 + q) * TTN_KMAX + j] = cadd(sm.H[(i0 + q) * TTN_KMAX + j], sm.bc[q]);
+                    }
+                __syncthreads();
             }
-            __syncthreads();
+            count_flops(16.0 * (double)S * (j + 1));
             for (int64_t e = threadIdx.x; e < S; e += kThreads) {
-                double2 acc = cd(w[e]);
-                for (int i = 0; i <= j; ++i) acc = csub(acc, cmul(sm.dots[i], cd(V[(int64_t)i * smax + e])));
-                w[e] = cT<TB>(acc);
+                TB acc = w[e];
+                for (int i = 0; i <= j; ++i) {
+                    const double2 h = sm.dots[i];
+                    cfma(acc, cT<TB>(make_double2(-h.x, -h.y)), V[(int64_t)i * smax + e]);
+                }
+                w[e] = acc;
             }
             __syncthreads();
         }
@@ -467,28 +656,32 @@ __device__ int krylov_once(TS* x, const Shape& sh, const TtnEntry* es, int ne, c
             for (int i = 0; i + 1 < j; ++i) sm.H[i * TTN_KMAX + j] = make_double2(0.0, 0.0);
             if (j > 0) sm.H[(j - 1) * TTN_KMAX + j] = sm.H[j * TTN_KMAX + (j - 1)];
         }
-        double2 nw = make_double2(0.0, 0.0);
-        for (int64_t e = threadIdx.x; e < S; e += kThreads) nw.x += cabs2(cd(w[e]));
-        const double hnext = sqrt(block_sum(nw, sm).x);
+        TB nwt = czero<TB>();
+        for (int64_t e = threadIdx.x; e < S; e += kThreads) cfmaconj(nwt, w[e], w[e]);
+        const double hnext = sqrt(block_sum(cd(nwt), sm).x);
         if (threadIdx.x == 0) sm.H[(j + 1) * TTN_KMAX + j] = make_double2(hnext, 0.0);
         __syncthreads();
+        sub_stop(1, tgs);
         const int mm = j + 1;
+        const long long te = sub_start();
         small_expm(sm, mm, tau, herm != 0);
         __syncthreads();
+        sub_stop(2, te);
         const double err = hnext * sqrt(cabs2(sm.y[j]));
         if (!isfinite(hnext) || !isfinite(err)) return -1;
         if (err <= tol || hnext == 0.0) {
             const double2 y0 = sm.y[0];
+            count_flops(8.0 * (double)S * mm);
             for (int64_t e = threadIdx.x; e < S; e += kThreads) {
-                double2 acc = make_double2(0.0, 0.0);
-                for (int i = 1; i < mm; ++i) acc = cadd(acc, cmul(sm.y[i], cd(V[(int64_t)i * smax + e])));
-                x[e] = cT<TS>(cadd(cmul(y0, cd(x[e])), cscale(acc, beta0)));
+                TB acc = czero<TB>();
+                for (int i = 1; i < mm; ++i) cfma(acc, cT<TB>(sm.y[i]), V[(int64_t)i * smax + e]);
+                x[e] = cT<TS>(cadd(cmul(y0, cd(x[e])), cscale(cd(acc), beta0)));
             }
             __syncthreads();
             return 1;
         }
         const double inv = 1.0 / hnext;
-        for (int64_t e = threadIdx.x; e < S; e += kThreads) w[e] = cT<TB>(cscale(cd(w[e]), inv));
+        for (int64_t e = threadIdx.x; e < S; e += kThreads) w[e] = cT<TB>(cscale(cd(w[e]), inv));   // (kept exact in FP64 mode)
         __syncthreads();
     }
     return 0;
@@ -516,8 +709,10 @@ __device__ int krylov_expm(TS* x, const Shape& sh, const TtnEntry* es, int ne, c
 template <class TB, class TS>
 __device__ const TB* as_bulk(const TS* a, TB* buf, int64_t n) {
     if (sizeof(TS) == sizeof(TB)) return (const TB*)a;
+    const long long t0 = sub_start();
     for (int64_t i = threadIdx.x; i < n; i += kThreads) buf[i] = cT<TB>(cd(a[i]));
     __syncthreads();
+    sub_stop(4, t0);
     return buf;
 }
 
@@ -653,27 +848,41 @@ __device__ void run_op(const TtnOp& op, const TtnInstance& in, double dt, Smem& 
 }
 
 template <class TS, class TB>
-__global__ void __launch_bounds__(kThreads) program_kernel(const TtnInstance* insts, int n_inst, double dt, int nrep) {
+__global__ void __launch_bounds__(kThreads, 1) program_kernel(const TtnInstance* insts, int n_inst, double dt, int nrep) {
     __shared__ Smem sm;
     const int b = blockIdx.x;
     if (b >= n_inst) return;
     const TtnInstance in = insts[b];
+    if (threadIdx.x == 0) { s_flops = 0.0; for (int i = 0; i < 8; ++i) s_sub[i] = 0; }
+    __syncthreads();
     for (int rep = 0; rep < nrep; ++rep) {
         for (int o = 0; o < in.n_ops; ++o) {
             if (threadIdx.x == 0) sm.flag = *((volatile int*)in.status);
             __syncthreads();
-            if (sm.flag != 0) return;
+            if (sm.flag != 0) break;
             const TtnOp op = in.ops[o];
+            const long long c0 = clock64();
             run_op<TS, TB>(op, in, dt, sm);
+            if (threadIdx.x == 0 && in.op_cycles) atomicAdd(&in.op_cycles[op.type & 15], (unsigned long long)(clock64() - c0));
         }
+        if (sm.flag != 0) break;
     }
+    if (threadIdx.x == 0 && in.flops) atomicAdd(in.flops, s_flops);
+    if (threadIdx.x == 0 && in.op_cycles)
+        for (int i = 0; i < 8; ++i) atomicAdd(&in.op_cycles[16 + i], s_sub[i]);
 }
 
 }  // namespace
 
 int ttn_launch_program(int precision, const TtnInstance* d_insts, int n_inst, double dt, int nrep, cudaStream_t s) {
     if (n_inst <= 0) return 0;
-    if (precision == 0) program_kernel<double2, double2><<<n_inst, kThreads, 0, s>>>(d_insts, n_inst, dt, nrep);
-    else program_kernel<double2, float2><<<n_inst, kThreads, 0, s>>>(d_insts, n_inst, dt, nrep);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(program_kernel<double2, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStageBytes);
+        cudaFuncSetAttribute(program_kernel<double2, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStageBytes);
+        attr_set = true;
+    }
+    if (precision == 0) program_kernel<double2, double2><<<n_inst, kThreads, kStageBytes, s>>>(d_insts, n_inst, dt, nrep);
+    else program_kernel<double2, float2><<<n_inst, kThreads, kStageBytes, s>>>(d_insts, n_inst, dt, nrep);
     return (int)cudaGetLastError();
 }

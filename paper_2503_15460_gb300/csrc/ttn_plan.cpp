@@ -173,9 +173,22 @@ struct Builder {
     const Tree& t;
     const Hamiltonian* h;
     Plan& p;
+    // Grouping direction per bond (edge to the parent): terms acting on both
+    // sides of the bond are summed either by their common outside factor
+    // (UPGRP: the up channel is sum_r c_r (inside part of r), paper Sec.
+    // II.B.2 term (C)) or by their common inside factor (DNGRP: the down
+    // channel is the sum of outside parts, term (B)), whichever gives fewer
+    // channels.
+    enum { NONE = 0, UPGRP = 1, DNGRP = 2 };
+    std::vector<int> dir;
+    std::vector<char> has_in, has_out;           // some term entirely inside / outside the subtree
     std::vector<int> up_loc, down_loc, phys_loc;
-    std::vector<std::map<Key, int>> up_prod, down_prod;
+    std::vector<std::map<Key, int>> up_prod, down_prod, up_grp, down_grp, phys_grp;
     std::vector<std::map<int, int>> phys_mat;
+    struct Pending { int kind; int c; Key key; int slot; };
+    enum { K_UP_LOC, K_UP_PROD, K_UP_GRP, K_DOWN_LOC, K_DOWN_PROD, K_DOWN_GRP };
+    std::vector<Pending> todo;
+    std::vector<std::vector<Proto>> up_entries, down_entries;   // per bond
     int one_slot = -1;     // 1x1 matrix holding 1 (root Gram matrix)
 
     Builder(const Tree& t_, const Hamiltonian* h_, Plan& p_) : t(t_), h(h_), p(p_) {}
@@ -191,7 +204,6 @@ struct Builder {
         p.slots[id].data = data;
         return id;
     }
-
     Key restrict_to(const Key& k, int c, bool inside) const {
         Key out;
         for (auto& f : k) if (t.in_sub(f.first, c) == inside) out.push_back(f);
@@ -211,33 +223,279 @@ struct Builder {
         for (auto& f : key) if (mode_of(z, f.first) == mode) out.push_back(f);
         return out;
     }
-    // slot of the up channel of mode k of node z for a (non-empty) restriction
-    int child_up(int z, int k, const Key& key) const {
-        if (t.leaf(z)) return phys_mat[z].at(key.at(0).second);
-        return up_prod[t.ch[z][k]].at(key);
+    std::set<int> modes_of(int z, const Key& key) const {
+        std::set<int> m;
+        for (auto& f : key) m.insert(mode_of(z, f.first));
+        return m;
     }
-    int child_loc(int z, int k) const {
-        if (t.leaf(z)) return phys_loc[z];
-        return up_loc[t.ch[z][k]];
+
+    // ---- channels (created on first use, defined by the closure loop) -----
+    int chan(std::map<Key, int>& m, int kind, int c, const Key& key) {
+        auto it = m.find(key);
+        if (it != m.end()) return it->second;
+        int s = new_slot(t.bond[c], t.bond[c]);
+        m[key] = s;
+        todo.push_back({kind, c, key, s});
+        return s;
+    }
+    int get_up_prod(int c, const Key& key) { return chan(up_prod[c], K_UP_PROD, c, key); }
+    int get_down_prod(int c, const Key& key) { return chan(down_prod[c], K_DOWN_PROD, c, key); }
+    int get_up_grp(int c, const Key& key) { return chan(up_grp[c], K_UP_GRP, c, key); }
+    int get_down_grp(int c, const Key& key) { return chan(down_grp[c], K_DOWN_GRP, c, key); }
+    int get_up_loc(int c) {
+        if (up_loc[c] < 0) { up_loc[c] = new_slot(t.bond[c], t.bond[c]); todo.push_back({K_UP_LOC, c, {}, up_loc[c]}); }
+        return up_loc[c];
+    }
+    int get_down_loc(int c) {
+        if (down_loc[c] < 0) { down_loc[c] = new_slot(t.bond[c], t.bond[c]); todo.push_back({K_DOWN_LOC, c, {}, down_loc[c]}); }
+        return down_loc[c];
+    }
+    int get_phys_mat(int l, int m) {
+        auto it = phys_mat[l].find(m);
+        if (it != phys_mat[l].end()) return it->second;
+        int d = t.phys[l];
+        return phys_mat[l][m] = const_slot(d, d, h->mats[m]);
+    }
+    // sum_{r: straddling leaf l, outside part == D} c_r M_r  (constant)
+    int get_phys_grp(int l, const Key& D) {
+        auto it = phys_grp[l].find(D);
+        if (it != phys_grp[l].end()) return it->second;
+        int d = t.phys[l];
+        std::vector<cplx> sum(d * d, 0.0);
+        for (size_t r = 0; r < h->terms.size(); ++r) {
+            const Key& key = h->terms[r];
+            Key in = restrict_to(key, l, true), out = restrict_to(key, l, false);
+            if (in.empty() || out != D) continue;
+            for (int i = 0; i < d * d; ++i) sum[i] += h->coeff[r] * h->mats[in[0].second][i];
+        }
+        return phys_grp[l][D] = const_slot(d, d, sum);
+    }
+    // up channel on mode k of node z for an individual inside part
+    int child_up_prod(int z, int k, const Key& part) {
+        if (t.leaf(z)) return get_phys_mat(z, part.at(0).second);
+        return get_up_prod(t.ch[z][k], part);
+    }
+
+    // Accumulator for one operator: group entries are added once (their
+    // coefficients live in the group channel), individual entries are summed.
+    struct Acc {
+        std::set<std::vector<int>> grp;
+        std::map<std::vector<int>, cplx> ind;
+        void add(bool group, const std::vector<int>& s, cplx w) {
+            if (group) grp.insert(s);
+            else ind[s] += w;
+        }
+        std::vector<Proto> out(int out_slot) const {
+            std::vector<Proto> es;
+            for (auto& s : grp) { Proto e; e.w = 1.0; e.out = out_slot; e.slot = s; es.push_back(e); }
+            for (auto& kv : ind) {
+                if (kv.second == cplx(0.0)) continue;
+                Proto e; e.w = kv.second; e.out = out_slot; e.slot = kv.first; es.push_back(e);
+            }
+            return es;
+        }
+    };
+
+    // Entry of term `key` (coefficient w) on node z when it touches >= 2 of
+    // z's modes.  The choice depends only on the set of touched modes, so
+    // every member of a group channel is routed to the same entry.
+    void term_entry(int z, const Key& key, cplx w, Acc& acc) {
+        const int D = (int)t.dims[z].size(), P = D - 1;
+        std::set<int> T = modes_of(z, key);
+        std::vector<int> sl(D, -1);
+        auto fill_rest = [&](int skip_mode) {
+            for (int j : T) {
+                if (j == skip_mode) continue;
+                Key part = restrict_mode(z, key, j);
+                sl[j] = (j == P) ? get_down_prod(z, part) : child_up_prod(z, j, part);
+            }
+        };
+        if (t.leaf(z)) {
+            // modes {0 (physical), P}
+            if (dir[z] == UPGRP) {
+                Key Dk = restrict_to(key, z, false);
+                sl[0] = get_phys_grp(z, Dk);
+                sl[P] = get_down_prod(z, Dk);
+                acc.add(true, sl, 1.0);
+                return;
+            }
+            if (dir[z] == DNGRP) {
+                Key U = restrict_to(key, z, true);
+                sl[P] = get_down_grp(z, U);
+                sl[0] = get_phys_mat(z, U.at(0).second);
+                acc.add(true, sl, 1.0);
+                return;
+            }
+            fill_rest(-1);
+            acc.add(false, sl, w);
+            return;
+        }
+        for (int k : T) {
+            if (k == P || dir[t.ch[z][k]] != UPGRP) continue;
+            int c = t.ch[z][k];
+            sl[k] = get_up_grp(c, restrict_to(key, c, false));
+            fill_rest(k);
+            acc.add(true, sl, 1.0);
+            return;
+        }
+        if (T.count(P) && z > 0 && dir[z] == DNGRP) {
+            sl[P] = get_down_grp(z, restrict_to(key, z, true));
+            fill_rest(P);
+            acc.add(true, sl, 1.0);
+            return;
+        }
+        fill_rest(-1);
+        acc.add(false, sl, w);
+    }
+
+    void define(const Pending& q) {
+        const int c = q.c;
+        const int R = (int)h->terms.size();
+        Acc acc;
+        if (q.kind == K_UP_LOC || q.kind == K_UP_PROD || q.kind == K_UP_GRP) {
+            // built at node c from its children (or its physical index)
+            const int D = (int)t.dims[c].size();
+            std::vector<int> sl(D, -1);
+            if (q.kind == K_UP_LOC) {
+                if (t.leaf(c)) { sl[0] = phys_loc[c]; acc.add(true, sl, 1.0); }
+                else {
+                    for (size_t k = 0; k < t.ch[c].size(); ++k)
+                        if (has_in[t.ch[c][k]]) { std::vector<int> s2(D, -1); s2[k] = get_up_loc(t.ch[c][k]); acc.add(true, s2, 1.0); }
+                    for (int r = 0; r < R; ++r) {
+                        const Key& key = h->terms[r];
+                        if (key.empty() || !restrict_to(key, c, false).empty()) continue;
+                        if (modes_of(c, key).size() < 2) continue;
+                        term_entry(c, key, h->coeff[r], acc);
+                    }
+                }
+            } else if (q.kind == K_UP_PROD) {
+                if (t.leaf(c)) sl[0] = get_phys_mat(c, q.key.at(0).second);
+                else for (int k : modes_of(c, q.key)) sl[k] = get_up_prod(t.ch[c][k], restrict_mode(c, q.key, k));
+                acc.add(true, sl, 1.0);
+            } else {  // K_UP_GRP: sum_{r: out^c_r == key} c_r (inside part)
+                if (t.leaf(c)) { sl[0] = get_phys_grp(c, q.key); acc.add(true, sl, 1.0); }
+                else {
+                    for (int r = 0; r < R; ++r) {
+                        const Key& key = h->terms[r];
+                        Key in = restrict_to(key, c, true);
+                        if (in.empty() || restrict_to(key, c, false) != q.key) continue;
+                        std::set<int> T = modes_of(c, in);
+                        std::vector<int> s2(D, -1);
+                        if (T.size() == 1) {
+                            int k = *T.begin();
+                            int ck = t.ch[c][k];
+                            if (dir[ck] == UPGRP) { s2[k] = get_up_grp(ck, q.key); acc.add(true, s2, 1.0); }
+                            else { s2[k] = get_up_prod(ck, in); acc.add(false, s2, h->coeff[r]); }
+                            continue;
+                        }
+                        bool done = false;
+                        for (int k : T) {
+                            int ck = t.ch[c][k];
+                            if (dir[ck] != UPGRP) continue;
+                            s2[k] = get_up_grp(ck, restrict_to(key, ck, false));
+                            for (int j : T) if (j != k) s2[j] = get_up_prod(t.ch[c][j], restrict_mode(c, in, j));
+                            acc.add(true, s2, 1.0);
+                            done = true;
+                            break;
+                        }
+                        if (!done) {
+                            for (int j : T) s2[j] = get_up_prod(t.ch[c][j], restrict_mode(c, in, j));
+                            acc.add(false, s2, h->coeff[r]);
+                        }
+                    }
+                }
+            }
+            auto es = acc.out(q.slot);
+            up_entries[c].insert(up_entries[c].end(), es.begin(), es.end());
+            return;
+        }
+        // down channels of bond c: built at its parent z (child index k)
+        const int z = t.parent[c];
+        const int k = (int)(std::find(t.ch[z].begin(), t.ch[z].end(), c) - t.ch[z].begin());
+        const int D = (int)t.dims[z].size(), P = D - 1;
+        if (q.kind == K_DOWN_LOC) {
+            if (z > 0 && has_out[z]) { std::vector<int> s2(D, -1); s2[P] = get_down_loc(z); acc.add(true, s2, 1.0); }
+            for (size_t j = 0; j < t.ch[z].size(); ++j)
+                if ((int)j != k && has_in[t.ch[z][j]]) { std::vector<int> s2(D, -1); s2[j] = get_up_loc(t.ch[z][j]); acc.add(true, s2, 1.0); }
+            for (int r = 0; r < R; ++r) {
+                const Key& key = h->terms[r];
+                if (key.empty() || !restrict_to(key, c, true).empty()) continue;
+                if (modes_of(z, key).size() < 2) continue;
+                term_entry(z, key, h->coeff[r], acc);
+            }
+        } else if (q.kind == K_DOWN_PROD) {
+            std::vector<int> s2(D, -1);
+            for (int j : modes_of(z, q.key)) {
+                Key part = restrict_mode(z, q.key, j);
+                s2[j] = (j == P) ? get_down_prod(z, part) : get_up_prod(t.ch[z][j], part);
+            }
+            acc.add(true, s2, 1.0);
+        } else {  // K_DOWN_GRP: sum_{r: in^c_r == key} c_r (outside part)
+            for (int r = 0; r < R; ++r) {
+                const Key& key = h->terms[r];
+                Key out = restrict_to(key, c, false);
+                if (out.empty() || restrict_to(key, c, true) != q.key) continue;
+                std::set<int> T = modes_of(z, out);
+                std::vector<int> s2(D, -1);
+                if (T.size() == 1) {
+                    int j = *T.begin();
+                    if (j == P) {
+                        if (z > 0 && dir[z] == DNGRP) { s2[P] = get_down_grp(z, q.key); acc.add(true, s2, 1.0); }
+                        else { s2[P] = get_down_prod(z, out); acc.add(false, s2, h->coeff[r]); }
+                    } else {
+                        int cj = t.ch[z][j];
+                        if (dir[cj] == UPGRP) { s2[j] = get_up_grp(cj, q.key); acc.add(true, s2, 1.0); }
+                        else { s2[j] = get_up_prod(cj, out); acc.add(false, s2, h->coeff[r]); }
+                    }
+                    continue;
+                }
+                bool done = false;
+                for (int j : T) {
+                    if (j == P || dir[t.ch[z][j]] != UPGRP) continue;
+                    int cj = t.ch[z][j];
+                    s2[j] = get_up_grp(cj, restrict_to(key, cj, false));
+                    for (int i : T) if (i != j) { Key part = restrict_mode(z, out, i); s2[i] = (i == P) ? get_down_prod(z, part) : get_up_prod(t.ch[z][i], part); }
+                    acc.add(true, s2, 1.0);
+                    done = true;
+                    break;
+                }
+                if (!done && T.count(P) && z > 0 && dir[z] == DNGRP) {
+                    s2[P] = get_down_grp(z, restrict_to(key, z, true));
+                    for (int i : T) if (i != P) s2[i] = get_up_prod(t.ch[z][i], restrict_mode(z, out, i));
+                    acc.add(true, s2, 1.0);
+                    done = true;
+                }
+                if (!done) {
+                    for (int i : T) { Key part = restrict_mode(z, out, i); s2[i] = (i == P) ? get_down_prod(z, part) : get_up_prod(t.ch[z][i], part); }
+                    acc.add(false, s2, h->coeff[r]);
+                }
+            }
+        }
+        auto es = acc.out(q.slot);
+        down_entries[c].insert(down_entries[c].end(), es.begin(), es.end());
+    }
+
+    void close() {
+        while (!todo.empty()) {
+            Pending q = todo.back();
+            todo.pop_back();
+            define(q);
+        }
     }
 
     void make_channels() {
         int n = t.n;
+        dir.assign(n, NONE);
+        has_in.assign(n, 0); has_out.assign(n, 0);
         up_loc.assign(n, -1); down_loc.assign(n, -1); phys_loc.assign(n, -1);
-        up_prod.assign(n, {}); down_prod.assign(n, {}); phys_mat.assign(n, {});
+        up_prod.assign(n, {}); down_prod.assign(n, {}); up_grp.assign(n, {}); down_grp.assign(n, {});
+        phys_grp.assign(n, {}); phys_mat.assign(n, {});
+        up_entries.assign(n, {}); down_entries.assign(n, {});
         if (!h) return;
         const int R = (int)h->terms.size();
-        // physical factor matrices and per-leaf local sums
         std::vector<std::vector<cplx>> loc_sum(n);
         for (int r = 0; r < R; ++r) {
             const Key& key = h->terms[r];
-            for (auto& f : key) {
-                int l = f.first, m = f.second;
-                if (!phys_mat[l].count(m)) {
-                    int d = t.phys[l];
-                    phys_mat[l][m] = const_slot(d, d, h->mats[m]);
-                }
-            }
             if (key.size() == 1) {
                 int l = key[0].first, d = t.phys[l];
                 if (loc_sum[l].empty()) loc_sum[l].assign(d * d, 0.0);
@@ -246,156 +504,63 @@ struct Builder {
         }
         for (int l = 0; l < n; ++l)
             if (!loc_sum[l].empty()) phys_loc[l] = const_slot(t.phys[l], t.phys[l], loc_sum[l]);
-        // bond channels
         for (int c = 1; c < n; ++c) {
-            int chi = t.bond[c];
+            std::set<Key> ins, outs;
             for (int r = 0; r < R; ++r) {
                 const Key& key = h->terms[r];
                 if (key.empty()) continue;
                 Key in = restrict_to(key, c, true), out = restrict_to(key, c, false);
-                if (!in.empty() && out.empty()) {
-                    if (up_loc[c] < 0) up_loc[c] = new_slot(chi, chi);
-                } else if (in.empty() && !out.empty()) {
-                    if (down_loc[c] < 0) down_loc[c] = new_slot(chi, chi);
-                } else {
-                    if (!up_prod[c].count(in)) up_prod[c][in] = new_slot(chi, chi);
-                    if (!down_prod[c].count(out)) down_prod[c][out] = new_slot(chi, chi);
-                }
+                if (!in.empty() && out.empty()) has_in[c] = 1;
+                else if (in.empty() && !out.empty()) has_out[c] = 1;
+                else { ins.insert(in); outs.insert(out); }
             }
+            if (!ins.empty()) dir[c] = outs.size() <= ins.size() ? UPGRP : DNGRP;
         }
     }
 
-    // ---- entry lists --------------------------------------------------------
-    std::vector<Proto> up_build(int z) {
-        std::vector<Proto> es;
-        int D = (int)t.dims[z].size();
-        auto blank = [&](int out) { Proto e; e.w = 1.0; e.out = out; e.slot.assign(D, -1); return e; };
-        if (up_loc[z] >= 0) {
-            if (t.leaf(z)) {
-                Proto e = blank(up_loc[z]); e.slot[0] = phys_loc[z]; es.push_back(e);
-            } else {
-                for (size_t k = 0; k < t.ch[z].size(); ++k)
-                    if (up_loc[t.ch[z][k]] >= 0) { Proto e = blank(up_loc[z]); e.slot[k] = up_loc[t.ch[z][k]]; es.push_back(e); }
-                for (size_t r = 0; r < h->terms.size(); ++r) {
-                    const Key& key = h->terms[r];
-                    if (key.empty() || !std::all_of(key.begin(), key.end(), [&](auto& f) { return t.in_sub(f.first, z); })) continue;
-                    std::set<int> modes;
-                    for (auto& f : key) modes.insert(mode_of(z, f.first));
-                    if (modes.size() < 2) continue;
-                    Proto e = blank(up_loc[z]); e.w = h->coeff[r];
-                    for (int k : modes) e.slot[k] = child_up(z, k, restrict_mode(z, key, k));
-                    es.push_back(e);
-                }
-            }
-        }
-        for (auto& kv : up_prod[z]) {
-            Proto e = blank(kv.second);
-            if (t.leaf(z)) e.slot[0] = phys_mat[z].at(kv.first.at(0).second);
-            else {
-                std::set<int> modes;
-                for (auto& f : kv.first) modes.insert(mode_of(z, f.first));
-                for (int k : modes) e.slot[k] = child_up(z, k, restrict_mode(z, kv.first, k));
-            }
-            es.push_back(e);
-        }
-        return es;
-    }
-
-    std::vector<Proto> down_build(int z, int k) {
-        std::vector<Proto> es;
-        int c = t.ch[z][k];
-        int D = (int)t.dims[z].size();
-        auto blank = [&](int out) { Proto e; e.w = 1.0; e.out = out; e.slot.assign(D, -1); return e; };
-        if (down_loc[c] >= 0) {
-            if (z > 0 && down_loc[z] >= 0) { Proto e = blank(down_loc[c]); e.slot[D - 1] = down_loc[z]; es.push_back(e); }
-            for (size_t j = 0; j < t.ch[z].size(); ++j)
-                if ((int)j != k && up_loc[t.ch[z][j]] >= 0) { Proto e = blank(down_loc[c]); e.slot[j] = up_loc[t.ch[z][j]]; es.push_back(e); }
-            for (size_t r = 0; r < h->terms.size(); ++r) {
-                const Key& key = h->terms[r];
-                if (key.empty() || std::any_of(key.begin(), key.end(), [&](auto& f) { return t.in_sub(f.first, c); })) continue;
-                std::set<int> modes;
-                for (auto& f : key) modes.insert(mode_of(z, f.first));
-                if (modes.size() < 2) continue;
-                Proto e = blank(down_loc[c]); e.w = h->coeff[r];
-                for (int m : modes) {
-                    Key part = restrict_mode(z, key, m);
-                    e.slot[m] = (m == D - 1) ? down_prod[z].at(part) : child_up(z, m, part);
-                }
-                es.push_back(e);
-            }
-        }
-        for (auto& kv : down_prod[c]) {
-            Proto e = blank(kv.second);
-            std::set<int> modes;
-            for (auto& f : kv.first) modes.insert(mode_of(z, f.first));
-            for (int m : modes) {
-                Key part = restrict_mode(z, kv.first, m);
-                e.slot[m] = (m == D - 1) ? down_prod[z].at(part) : child_up(z, m, part);
-            }
-            es.push_back(e);
-        }
-        return es;
-    }
-
+    // ---- operator entry lists ------------------------------------------------
     std::vector<Proto> heff_terms(int z) {
-        std::vector<Proto> es;
-        int D = (int)t.dims[z].size();
-        auto blank = [&]() { Proto e; e.w = 1.0; e.out = -1; e.slot.assign(D, -1); return e; };
+        Acc acc;
+        const int D = (int)t.dims[z].size(), P = D - 1;
         int nchild = t.leaf(z) ? 1 : (int)t.ch[z].size();
-        for (int k = 0; k < nchild; ++k)
-            if (child_loc(z, k) >= 0) { Proto e = blank(); e.slot[k] = child_loc(z, k); es.push_back(e); }
-        if (z > 0 && down_loc[z] >= 0) { Proto e = blank(); e.slot[D - 1] = down_loc[z]; es.push_back(e); }
+        for (int k = 0; k < nchild; ++k) {
+            std::vector<int> sl(D, -1);
+            if (t.leaf(z)) { if (phys_loc[z] < 0) continue; sl[0] = phys_loc[z]; }
+            else { if (!has_in[t.ch[z][k]]) continue; sl[k] = get_up_loc(t.ch[z][k]); }
+            acc.add(true, sl, 1.0);
+        }
+        if (z > 0 && has_out[z]) { std::vector<int> sl(D, -1); sl[P] = get_down_loc(z); acc.add(true, sl, 1.0); }
         for (size_t r = 0; r < h->terms.size(); ++r) {
             const Key& key = h->terms[r];
-            if (key.empty()) { Proto e = blank(); e.w = h->coeff[r]; es.push_back(e); continue; }
-            std::set<int> modes;
-            for (auto& f : key) modes.insert(mode_of(z, f.first));
-            if (modes.size() < 2) continue;
-            Proto e = blank(); e.w = h->coeff[r];
-            for (int m : modes) {
-                Key part = restrict_mode(z, key, m);
-                e.slot[m] = (m == D - 1) ? down_prod[z].at(part) : child_up(z, m, part);
-            }
-            es.push_back(e);
+            if (key.empty()) { acc.add(false, std::vector<int>(D, -1), h->coeff[r]); continue; }
+            if (modes_of(z, key).size() < 2) continue;
+            term_entry(z, key, h->coeff[r], acc);
         }
-        return es;
+        return acc.out(-1);
     }
 
     std::vector<Proto> bond_terms(int c) {
-        std::vector<Proto> es;
-        auto blank = [&]() { Proto e; e.w = 1.0; e.out = -1; e.slot.assign(2, -1); return e; };
-        if (up_loc[c] >= 0) { Proto e = blank(); e.slot[0] = up_loc[c]; es.push_back(e); }
-        if (down_loc[c] >= 0) { Proto e = blank(); e.slot[1] = down_loc[c]; es.push_back(e); }
+        Acc acc;
+        if (has_in[c]) acc.add(true, {get_up_loc(c), -1}, 1.0);
+        if (has_out[c]) acc.add(true, {-1, get_down_loc(c)}, 1.0);
         for (size_t r = 0; r < h->terms.size(); ++r) {
             const Key& key = h->terms[r];
-            if (key.empty()) { Proto e = blank(); e.w = h->coeff[r]; es.push_back(e); continue; }
+            if (key.empty()) { acc.add(false, {-1, -1}, h->coeff[r]); continue; }
             Key in = restrict_to(key, c, true), out = restrict_to(key, c, false);
             if (in.empty() || out.empty()) continue;
-            Proto e = blank(); e.w = h->coeff[r];
-            e.slot[0] = up_prod[c].at(in);
-            e.slot[1] = down_prod[c].at(out);
-            es.push_back(e);
+            if (dir[c] == UPGRP) acc.add(true, {get_up_grp(c, out), get_down_prod(c, out)}, 1.0);
+            else if (dir[c] == DNGRP) acc.add(true, {get_up_prod(c, in), get_down_grp(c, in)}, 1.0);
+            else acc.add(false, {get_up_prod(c, in), get_down_prod(c, out)}, h->coeff[r]);
         }
-        return es;
+        return acc.out(-1);
     }
 
-    // Merge identical entries, then repeatedly combine entries that differ
-    // in exactly one mode into one entry whose factor on that mode is a
-    // linear combination (a "combo" slot, evaluated by COMBO ops).
+    // Repeatedly combine entries that differ in exactly one mode into one
+    // entry whose factor on that mode is a linear combination (a "combo"
+    // slot, evaluated by COMBO ops right before the operator is applied).
     std::vector<Proto> combine(std::vector<Proto> es, const std::vector<int>& dims,
                                std::vector<std::vector<Proto>>& combo_rounds) {
         int D = (int)dims.size();
-        {
-            std::map<std::pair<int, std::vector<int>>, size_t> seen;
-            std::vector<Proto> out;
-            for (auto& e : es) {
-                auto key = std::make_pair(e.out, e.slot);
-                auto it = seen.find(key);
-                if (it == seen.end()) { seen[key] = out.size(); out.push_back(e); }
-                else out[it->second].w += e.w;
-            }
-            es.swap(out);
-        }
         for (int round = 0; round < 4 * D; ++round) {
             int best = -1; size_t best_gain = 0;
             for (int j = 0; j < D; ++j) {
@@ -476,20 +641,28 @@ struct Builder {
         heff_combo.assign(n, {}); bond_combo.assign(n, {});
         heff_rng.assign(n, {0, 0}); bond_rng.assign(n, {0, 0}); up_rng.assign(n, {0, 0});
         down_rng.assign(n, {});
+        std::vector<std::vector<Proto>> heff(n), bond(n);
+        for (int z = 0; z < n; ++z) {
+            heff[z] = heff_terms(z);
+            if (z > 0) bond[z] = bond_terms(z);
+        }
+        close();
         for (int z = 0; z < n; ++z) {
             std::vector<std::vector<Proto>> rounds;
-            auto es = combine(heff_terms(z), t.dims[z], rounds);
+            auto es = combine(heff[z], t.dims[z], rounds);
             for (auto& rd : rounds) heff_combo[z].push_back(push_entries(rd));
             heff_rng[z] = push_entries(es);
             if (z > 0) {
                 std::vector<std::vector<Proto>> br;
-                auto bs = combine(bond_terms(z), {t.bond[z], t.bond[z]}, br);
+                auto bs = combine(bond[z], {t.bond[z], t.bond[z]}, br);
                 for (auto& rd : br) bond_combo[z].push_back(push_entries(rd));
                 bond_rng[z] = push_entries(bs);
-                up_rng[z] = push_entries(up_build(z));
+                up_rng[z] = push_entries(up_entries[z]);
             }
-            if (!t.leaf(z))
-                for (size_t k = 0; k < t.ch[z].size(); ++k) down_rng[z].push_back(push_entries(down_build(z, (int)k)));
+        }
+        for (int z = 0; z < n; ++z) {
+            if (t.leaf(z)) continue;
+            for (size_t k = 0; k < t.ch[z].size(); ++k) down_rng[z].push_back(push_entries(down_entries[t.ch[z][k]]));
         }
     }
 
@@ -713,6 +886,8 @@ std::string make_plan(const Tree& t, const Hamiltonian* h, int precision, Plan& 
     off = align_up(off + (int64_t)(TTN_KMAX + 3) * p.smax * (int64_t)p.esz + 2 * p.smax * 16, 256);
     p.status_off = off; off += 64;
     p.steps_off = off; off += 64;
+    p.flops_off = off; off += 64;
+    p.cycles_off = off; off += 32 * 8;
     p.scal_off = off; off = align_up(off + 16 * 16, 256);
     p.max_stamps = 4096;
     p.stamps_off = off; off = align_up(off + 8 * (int64_t)p.max_stamps, 256);

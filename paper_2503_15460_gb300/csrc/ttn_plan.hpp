@@ -66,7 +66,7 @@ struct Plan {
     size_t esz = 16;                 // bytes per complex element of the bulk type (slots, Krylov)
     size_t esz_state = 16;           // bytes per element of node tensors / bond buffer (complex128)
     std::vector<int64_t> tensor_off;
-    int64_t bond_off = 0, work_off = 0, status_off = 0, steps_off = 0, stamps_off = 0, scal_off = 0;
+    int64_t bond_off = 0, work_off = 0, status_off = 0, steps_off = 0, stamps_off = 0, scal_off = 0, flops_off = 0, cycles_off = 0;
     int64_t smax = 0;                // elements per workspace vector
     int max_stamps = 0;
     int64_t total_bytes = 0;

@@ -71,6 +71,8 @@ struct TtnInstance {
     int* status;            // device status word (0 = ok, else ttn_status code)
     int* steps_done;        // device step counter
     unsigned long long* stamps;  // optional per-step completion time stamps (ns)
+    double* flops;          // algorithmic flop counter (accumulated by block thread 0)
+    unsigned long long* op_cycles;  // SM clock cycles spent per op type (16 counters)
     double ktol;
     double qtol;            // QR rank threshold relative to ||M||_F
     int kmax;

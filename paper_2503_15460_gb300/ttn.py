@@ -51,6 +51,11 @@ _sig = {
     "ttn_get_state": ([_P, _C128, _I64], C.c_int),
     "ttn_bond_dims": ([_P, _I32], C.c_int),
     "ttn_set_stream": ([_P, _P], C.c_int),
+    "ttn_set_device": ([C.c_int], C.c_int),
+    "ttn_op_cycles": ([_P, np.ctypeslib.ndpointer(dtype=np.uint64, flags="C_CONTIGUOUS")], C.c_int),
+    "ttn_step_stats": ([_P, C.POINTER(C.c_int64), C.POINTER(C.c_double),
+                        np.ctypeslib.ndpointer(dtype=np.uint64, flags="C_CONTIGUOUS"), C.c_int,
+                        C.POINTER(C.c_int)], C.c_int),
     "ttn_device_bytes": ([_P, C.POINTER(C.c_size_t)], C.c_int),
     "ttn_last_error": ([_P], C.c_char_p),
     "ttn_destroy": ([_P], None),
@@ -189,6 +194,30 @@ def ttn_bond_dims(ctx, n_nodes):
     out = np.zeros(n_nodes, dtype=np.int32)
     _check(_lib.ttn_bond_dims(ctx, out), ctx)
     return out
+
+
+OP_NAMES = {1: "qr_down", 2: "qr_up", 3: "absorb_child", 4: "absorb_parent", 5: "env", 6: "combo",
+            7: "evolve", 8: "dot", 9: "trace", 10: "contract_vec", 11: "step_end",
+            16: "in:heff", 17: "in:gram_schmidt", 18: "in:small_expm", 19: "in:gram", 20: "in:convert"}
+
+
+def ttn_op_cycles(ctx):
+    out = np.zeros(32, dtype=np.uint64)
+    _check(_lib.ttn_op_cycles(ctx, out), ctx)
+    return {OP_NAMES.get(i, str(i)): int(v) for i, v in enumerate(out) if v}
+
+
+def ttn_set_device(device: int):
+    _check(_lib.ttn_set_device(int(device)), None)
+
+
+def ttn_step_stats(ctx, max_stamps=4096):
+    steps = C.c_int64(0)
+    fl = C.c_double(0.0)
+    st = np.zeros(max(1, max_stamps), dtype=np.uint64)
+    n = C.c_int(0)
+    _check(_lib.ttn_step_stats(ctx, C.byref(steps), C.byref(fl), st, int(max_stamps), C.byref(n)), ctx)
+    return steps.value, fl.value, st[:n.value].copy()
 
 
 def ttn_set_stream(ctx, stream_handle: int):
