@@ -293,7 +293,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--batch", type=int, default=N_SM, help="instances per GPU")
+    ap.add_argument("--batch", type=int, default=2 * N_SM, help="instances per GPU (two thread blocks per SM)")
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--check-instances", type=int, default=2)
     ap.add_argument("--cpu-steps", type=int, default=1)

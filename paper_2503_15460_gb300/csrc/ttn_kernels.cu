@@ -231,7 +231,7 @@ template <class T>
 __device__ void mode_prod(T* __restrict__ out, const T* __restrict__ in, int64_t L, int nin, int nout,
                           int64_t R, const T* __restrict__ M, bool transM, double2 w, bool accumulate) {
     count_flops(8.0 * (double)(L * nout * R) * nin);
-    if (transM || nin != nout || nin > 32) {
+    if (transM || nin != nout || nin > (sizeof(T) == 16 ? 16 : 32)) {
         mode_prod_simple(out, in, L, nin, nout, R, M, transM, w, accumulate);
         return;
     }
@@ -240,8 +240,8 @@ __device__ void mode_prod(T* __restrict__ out, const T* __restrict__ in, int64_t
     else if (nin <= 8) mode_prod_tiled<T, 8>(out, in, L, nin, R, M, w, accumulate);
     else if (nin <= 12) mode_prod_tiled<T, 12>(out, in, L, nin, R, M, w, accumulate);
     else if (nin <= 16) mode_prod_tiled<T, 16>(out, in, L, nin, R, M, w, accumulate);
-    else if (nin <= 24) mode_prod_tiled<T, 24>(out, in, L, nin, R, M, w, accumulate);
-    else mode_prod_tiled<T, 32>(out, in, L, nin, R, M, w, accumulate);
+    else if (sizeof(T) == 8 && nin <= 24) mode_prod_tiled<T, (sizeof(T) == 8 ? 24 : 16)>(out, in, L, nin, R, M, w, accumulate);
+    else if (sizeof(T) == 8) mode_prod_tiled<T, (sizeof(T) == 8 ? 32 : 16)>(out, in, L, nin, R, M, w, accumulate);
 }
 
 template <class T>
@@ -279,27 +279,61 @@ __device__ const T* apply_chain(const T* src, T* t1, T* t2, const Shape& sh, con
     return cur;
 }
 
-// out = sum_e w_e (x_j M_ej) in   (effective Hamiltonian / bond operator)
+__device__ __forceinline__ int last_factor(const TtnEntry& e, int D) {
+    int lm = -1;
+    for (int j = 0; j < D; ++j) if (e.slot[j] >= 0) lm = j;
+    return lm;
+}
+__device__ __forceinline__ int n_factors(const TtnEntry& e, int D) {
+    int n = 0;
+    for (int j = 0; j < D; ++j) n += e.slot[j] >= 0;
+    return n;
+}
+
+// out = sum_e w_e (x_j M_ej) in   (effective Hamiltonian / bond operator).
+// Entries are ordered so that those sharing their last factor (highest mode
+// with a matrix, same slot) are adjacent; their partial chains are summed in
+// t3 and the shared factor is applied once.
 template <class T>
-__device__ void heff_apply(T* __restrict__ out, const T* __restrict__ in, T* t1, T* t2, const Shape& sh,
+__device__ void heff_apply(T* __restrict__ out, const T* __restrict__ in, T* t1, T* t2, T* t3, const Shape& sh,
                            const TtnEntry* es, int ne, const TtnSlot* slots) {
     const int64_t S = sh.size();
     for (int64_t i = threadIdx.x; i < S; i += kThreads) out[i] = czero<T>();
     __syncthreads();
-    for (int ei = 0; ei < ne; ++ei) {
-        const TtnEntry e = es[ei];
+    int i = 0;
+    while (i < ne) {
+        const TtnEntry e = es[i];
         const double2 w = make_double2(e.wr, e.wi);
-        bool any = false;
-        for (int j = 0; j < sh.D; ++j) any |= e.slot[j] >= 0;
-        if (!any) {
+        const int lm = last_factor(e, sh.D);
+        if (lm < 0) {
             const T wt = cT<T>(w);
-            for (int64_t i = threadIdx.x; i < S; i += kThreads) {
-                T o = out[i]; cfma(o, wt, in[i]); out[i] = o;
+            for (int64_t q = threadIdx.x; q < S; q += kThreads) {
+                T o = out[q]; cfma(o, wt, in[q]); out[q] = o;
             }
             __syncthreads();
+            ++i;
             continue;
         }
-        apply_chain(in, t1, t2, sh, e, slots, -1, out, w);
+        int j = i + 1;
+        if (n_factors(e, sh.D) >= 2)
+            while (j < ne && last_factor(es[j], sh.D) == lm && es[j].slot[lm] == e.slot[lm] &&
+                   n_factors(es[j], sh.D) >= 2) ++j;
+        if (j - i == 1) {
+            apply_chain(in, t1, t2, sh, e, slots, -1, out, w);
+            i = j;
+            continue;
+        }
+        for (int64_t q = threadIdx.x; q < S; q += kThreads) t3[q] = czero<T>();
+        __syncthreads();
+        for (int q = i; q < j; ++q) {
+            const TtnEntry eq = es[q];
+            apply_chain(in, t1, t2, sh, eq, slots, lm, t3, make_double2(eq.wr, eq.wi));
+        }
+        const int n = sh.d[lm];
+        mode_prod(out, (const T*)t3, sh.before(lm), n, n, sh.after(lm), (const T*)slots[e.slot[lm]].ptr, false,
+                  make_double2(1.0, 0.0), true);
+        __syncthreads();
+        i = j;
     }
 }
 
@@ -323,10 +357,10 @@ __device__ void gram_acc(T* G, const T* __restrict__ X, const T* __restrict__ Y,
     if (groups > 8) groups = 8;
     const int tid = threadIdx.x;
     const bool active = tid < ntile * groups || ntile > kThreads;
-    T acc[4][2][2];
+    T acc[2][2][2];
     const int nrep = (ntile + kThreads - 1) / kThreads;      // tiles per thread when chi > 32
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+    for (int q = 0; q < 2; ++q)
 #pragma unroll
         for (int i = 0; i < 2; ++i)
 #pragma unroll
@@ -351,7 +385,7 @@ __device__ void gram_acc(T* G, const T* __restrict__ X, const T* __restrict__ Y,
         __syncthreads();
         if (active) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
+            for (int q = 0; q < 2; ++q) {
                 if (q >= nrep) break;
                 const int tile = (ntile >= kThreads) ? tid + q * kThreads : tid % ntile;
                 if (tile >= ntile) break;
@@ -373,7 +407,7 @@ __device__ void gram_acc(T* G, const T* __restrict__ X, const T* __restrict__ Y,
     T* Pp = (T*)dyn_smem;
     if (active) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < 2; ++q) {
             if (q >= nrep) break;
             const int tile = (ntile >= kThreads) ? tid + q * kThreads : tid % ntile;
             if (tile >= ntile) break;
@@ -392,25 +426,51 @@ __device__ void gram_acc(T* G, const T* __restrict__ X, const T* __restrict__ Y,
     __syncthreads();
 }
 
-// Environment build: for every entry, out += w * Q^dag (x_{j != keep} M_j) Q.
+// Environment build: for every output slot, out = Q^dag (sum_e w_e x_{j != keep} M_ej) Q.
+// The chains of all entries of one output are summed in ysum first, so each
+// output costs one Gram contraction.
 template <class T>
-__device__ void env_build(const T* Q, T* t1, T* t2, const Shape& sh, int keep, const TtnEntry* es, int ne,
+__device__ void env_build(const T* Q, T* t1, T* t2, T* ysum, const Shape& sh, int keep, const TtnEntry* es, int ne,
                           const TtnSlot* slots) {
-    int prev = -1;
-    for (int ei = 0; ei < ne; ++ei) {
-        const TtnEntry e = es[ei];
-        T* out = (T*)slots[e.out].ptr;
-        if (e.out != prev) {
-            const int n = slots[e.out].rows * slots[e.out].cols;
-            for (int i = threadIdx.x; i < n; i += kThreads) out[i] = czero<T>();
+    const int64_t S = sh.size();
+    int i = 0;
+    while (i < ne) {
+        const int outs = es[i].out;
+        int j = i;
+        while (j < ne && es[j].out == outs) ++j;
+        T* out = (T*)slots[outs].ptr;
+        const int n = slots[outs].rows * slots[outs].cols;
+        for (int q = threadIdx.x; q < n; q += kThreads) out[q] = czero<T>();
+        const T* Y;
+        if (j - i == 1) {
+            const TtnEntry e = es[i];
+            Y = apply_chain(Q, t1, t2, sh, e, slots, keep, (T*)nullptr, make_double2(1.0, 0.0));
             __syncthreads();
-            prev = e.out;
+            const long long tg = sub_start();
+            gram_acc(out, Q, Y, sh, keep, make_double2(e.wr, e.wi));
+            sub_stop(3, tg);
+        } else {
+            for (int64_t q = threadIdx.x; q < S; q += kThreads) ysum[q] = czero<T>();
+            __syncthreads();
+            for (int q = i; q < j; ++q) {
+                const TtnEntry e = es[q];
+                const double2 w = make_double2(e.wr, e.wi);
+                bool any = false;
+                for (int m = 0; m < sh.D; ++m) any |= (m != keep && e.slot[m] >= 0);
+                if (!any) {
+                    const T wt = cT<T>(w);
+                    for (int64_t x = threadIdx.x; x < S; x += kThreads) { T o = ysum[x]; cfma(o, wt, Q[x]); ysum[x] = o; }
+                    __syncthreads();
+                } else {
+                    apply_chain(Q, t1, t2, sh, e, slots, keep, ysum, w);
+                }
+            }
+            const long long tg = sub_start();
+            gram_acc(out, Q, (const T*)ysum, sh, keep, make_double2(1.0, 0.0));
+            sub_stop(3, tg);
         }
-        const T* Y = apply_chain(Q, t1, t2, sh, e, slots, keep, (T*)nullptr, make_double2(1.0, 0.0));
-        const long long tg = sub_start();
-        gram_acc(out, Q, Y, sh, keep, make_double2(e.wr, e.wi));
-        sub_stop(3, tg);
         __syncthreads();
+        i = j;
     }
 }
 
@@ -541,7 +601,7 @@ __device__ __forceinline__ double2 qr_R(const double2* Wc, int64_t m, int a, int
 
 // ---------------------------------------------------------------------------
 // Small projected exponential: sm.y = exp(-i tau H_m) e_0 (warp 0).
-// Scaling into substeps of 1-norm <= 1/2, each summed as a Taylor series on
+// Scaling into substeps of 1-norm <= 1, each summed as a Taylor series on
 // the vector (Moler & Van Loan, "Nineteen dubious ways", method 1 with
 // scaling); for a tridiagonal H only the band is used.
 // ---------------------------------------------------------------------------
@@ -557,29 +617,26 @@ __device__ void small_expm(Smem& sm, int m, double tau, bool band) {
         __syncwarp();
         return;
     }
-    int s = (int)ceil(nrm / 0.5);
+    // substeps of 1-norm <= 1; 18 Taylor terms leave a truncation below 1/19! ~ 8e-18
+    int s = (int)ceil(nrm);
     if (s < 1) s = 1;
     const double h = tau / s;
     double2 y = make_double2(i == 0 ? 1.0 : 0.0, 0.0);
-    const int jlo = band ? max(0, i - 1) : max(0, i - 1);
+    const int jlo = max(0, i - 1);
     const int jhi = band ? min(m - 1, i + 1) : m - 1;
     for (int step = 0; step < s; ++step) {
         double2 term = y, acc = y;
-        for (int kk = 1; kk <= 40; ++kk) {
-            if (i < TTN_KMAX + 1) sm.u[i] = term;
+#pragma unroll 1
+        for (int kk = 1; kk <= 18; ++kk) {
+            sm.u[i] = term;
             __syncwarp();
             double2 nt = make_double2(0.0, 0.0);
             if (i < m)
                 for (int j = jlo; j <= jhi; ++j) nt = cadd(nt, cmul(sm.H[i * TTN_KMAX + j], sm.u[j]));
             __syncwarp();
-            // term <- (-i h / kk) * H term
             const double f = h / kk;
-            term = make_double2(nt.y * f, -nt.x * f);
-            if (i >= m) term = make_double2(0.0, 0.0);
+            term = (i < m) ? make_double2(nt.y * f, -nt.x * f) : make_double2(0.0, 0.0);
             acc = cadd(acc, term);
-            const double tmax = warp_max(sqrt(cabs2(term)));
-            const double amax = warp_max(sqrt(cabs2(acc)));
-            if (tmax <= 1e-18 * amax) break;
         }
         y = acc;
     }
@@ -601,7 +658,8 @@ __device__ void small_expm(Smem& sm, int m, double tau, bool band) {
 template <class TS, class TB>
 __device__ int krylov_once(TS* x, const Shape& sh, const TtnEntry* es, int ne, const TtnSlot* slots,
                            double tau, int herm, double tol, int kmax, TB* V, int64_t smax, TB* t1, TB* t2,
-                           Smem& sm) {
+                           TB* t3, Smem& sm) {
+    double logbound = 0.0;          // log(|tau|^m prod h_{i+1,i} / m!)
     const int64_t S = sh.size();
     double2 nb = make_double2(0.0, 0.0);
     for (int64_t i = threadIdx.x; i < S; i += kThreads) nb.x += cabs2(cd(x[i]));
@@ -618,7 +676,7 @@ __device__ int krylov_once(TS* x, const Shape& sh, const TtnEntry* es, int ne, c
         TB* vj = V + (int64_t)j * smax;
         TB* w = V + (int64_t)(j + 1) * smax;
         const long long th = sub_start();
-        heff_apply(w, vj, t1, t2, sh, es, ne, slots);
+        heff_apply(w, vj, t1, t2, t3, sh, es, ne, slots);
         sub_stop(0, th);
         const long long tgs = sub_start();
         for (int pass = 0; pass < 2; ++pass) {
@@ -663,12 +721,25 @@ __device__ int krylov_once(TS* x, const Shape& sh, const TtnEntry* es, int ne, c
         __syncthreads();
         sub_stop(1, tgs);
         const int mm = j + 1;
+        if (!isfinite(hnext)) return -1;
+        // For a Hermitian tridiagonal H_m, |e_m^T exp(-i tau H_m) e_1| <= |tau|^(m-1)
+        // prod_{i<m-1} h_{i+1,i} / (m-1)!, so h_{m+1,m} times that bounds Saad's
+        // estimate; the small exponential is evaluated only once this bound is
+        // within 1e4 of the tolerance (always at kmax and on breakdown).
+        logbound += log(fmax(hnext, 1e-300)) + log(fabs(tau) + 1e-300) - log((double)mm);
+        const bool near = logbound <= log(1e4 * tol) || j == kmax - 1 || hnext == 0.0 || (j & 3) == 3;
+        if (!near) {
+            const double inv = 1.0 / hnext;
+            for (int64_t e = threadIdx.x; e < S; e += kThreads) w[e] = cT<TB>(cscale(cd(w[e]), inv));
+            __syncthreads();
+            continue;
+        }
         const long long te = sub_start();
         small_expm(sm, mm, tau, herm != 0);
         __syncthreads();
         sub_stop(2, te);
         const double err = hnext * sqrt(cabs2(sm.y[j]));
-        if (!isfinite(hnext) || !isfinite(err)) return -1;
+        if (!isfinite(err)) return -1;
         if (err <= tol || hnext == 0.0) {
             const double2 y0 = sm.y[0];
             count_flops(8.0 * (double)S * mm);
@@ -690,11 +761,11 @@ __device__ int krylov_once(TS* x, const Shape& sh, const TtnEntry* es, int ne, c
 template <class TS, class TB>
 __device__ int krylov_expm(TS* x, const Shape& sh, const TtnEntry* es, int ne, const TtnSlot* slots,
                            double tau, int herm, double tol, int kmax, TB* V, int64_t smax, TB* t1, TB* t2,
-                           Smem& sm) {
+                           TB* t3, Smem& sm) {
     // substeps: halve the interval whenever kmax is reached (at most 2^12 pieces)
     int nsub = 1, done = 0;
     while (done < nsub) {
-        const int r = krylov_once(x, sh, es, ne, slots, tau / nsub, herm, tol, kmax, V, smax, t1, t2, sm);
+        const int r = krylov_once(x, sh, es, ne, slots, tau / nsub, herm, tol, kmax, V, smax, t1, t2, t3, sm);
         if (r < 0) return 0;
         if (r > 0) {
             ++done;
@@ -725,11 +796,11 @@ __device__ void run_op(const TtnOp& op, const TtnInstance& in, double dt, Smem& 
     sh.D = op.D;
     for (int j = 0; j < TTN_MAXD; ++j) sh.d[j] = j < op.D ? op.dims[j] : 1;
     TB* work = (TB*)in.work;
-    TB* V = work;
-    TB* t3 = work + (int64_t)TTN_KMAX * in.smax;        // last basis vector: free outside EVOLVE
+    TB* V = work;                                       // TTN_KMAX + 1 Krylov vectors
     TB* t1 = work + (int64_t)(TTN_KMAX + 1) * in.smax;
     TB* t2 = t1 + in.smax;
-    double2* Wc = (double2*)(t2 + in.smax);
+    TB* t3 = t2 + in.smax;
+    double2* Wc = (double2*)(t3 + in.smax);
     double2* Qc = Wc + in.smax;
     const TtnEntry* es = in.entries + op.e0;
     switch (op.type) {
@@ -781,9 +852,9 @@ __device__ void run_op(const TtnOp& op, const TtnInstance& in, double dt, Smem& 
         __syncthreads();
         break;
     }
-    case TTN_OP_ENV: {
-        const TB* Q = as_bulk<TB>((const TS*)op.a, t3, sh.size());
-        env_build(Q, t1, t2, sh, op.k, es, op.ne, in.slots);
+    case TTN_OP_ENV: {                // Krylov vectors are free here: V[0] holds Q, V[1] the chain sum
+        const TB* Q = as_bulk<TB>((const TS*)op.a, V, sh.size());
+        env_build(Q, t1, t2, V + in.smax, sh, op.k, es, op.ne, in.slots);
         break;
     }
     case TTN_OP_COMBO:
@@ -791,7 +862,7 @@ __device__ void run_op(const TtnOp& op, const TtnInstance& in, double dt, Smem& 
         break;
     case TTN_OP_EVOLVE: {
         const int ok = krylov_expm((TS*)op.a, sh, es, op.ne, in.slots, op.tau_coef * dt, op.hermitian, in.ktol,
-                                   in.kmax, V, in.smax, t1, t2, sm);
+                                   in.kmax, V, in.smax, t1, t2, t3, sm);
         if (!ok && threadIdx.x == 0) atomicExch(in.status, 4);   // TTN_E_NOCONV
         __syncthreads();
         break;
@@ -799,8 +870,8 @@ __device__ void run_op(const TtnOp& op, const TtnInstance& in, double dt, Smem& 
     case TTN_OP_DOT: {
         double2 r;
         if (op.ne > 0) {
-            const TB* A = as_bulk<TB>((const TS*)op.a, t3, sh.size());
-            heff_apply(t1, A, t2, V, sh, es, op.ne, in.slots);
+            const TB* A = as_bulk<TB>((const TS*)op.a, V, sh.size());
+            heff_apply(t1, A, t2, V + in.smax, t3, sh, es, op.ne, in.slots);
             r = block_dot(A, t1, sh.size(), sm);
         } else {
             const TS* A = (const TS*)op.a;
@@ -812,7 +883,7 @@ __device__ void run_op(const TtnOp& op, const TtnInstance& in, double dt, Smem& 
     }
     case TTN_OP_CONTRACT_VEC: {      // chain of rectangular mode products, result into slot k
         const TtnEntry e = es[0];
-        const TB* cur = as_bulk<TB>((const TS*)op.a, t3, sh.size());
+        const TB* cur = as_bulk<TB>((const TS*)op.a, t3, sh.size());   // t3 is not a chain buffer here
         Shape s2 = sh;
         for (int j = 0; j < sh.D; ++j) {
             if (e.slot[j] < 0) continue;
@@ -848,7 +919,7 @@ __device__ void run_op(const TtnOp& op, const TtnInstance& in, double dt, Smem& 
 }
 
 template <class TS, class TB>
-__global__ void __launch_bounds__(kThreads, 1) program_kernel(const TtnInstance* insts, int n_inst, double dt, int nrep) {
+__global__ void __launch_bounds__(kThreads, 2) program_kernel(const TtnInstance* insts, int n_inst, double dt, int nrep) {
     __shared__ Smem sm;
     const int b = blockIdx.x;
     if (b >= n_inst) return;

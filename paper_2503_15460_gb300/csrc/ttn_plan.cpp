@@ -598,10 +598,20 @@ struct Builder {
     }
 
     // ---- emission -----------------------------------------------------------
+    // Entries are ordered by output slot, then by their last factor (mode,
+    // slot) so that the device can share the last factor within a run.
     std::pair<int, int> push_entries(const std::vector<Proto>& es) {
         int e0 = (int)p.entries.size();
         std::vector<Proto> sorted = es;
-        std::stable_sort(sorted.begin(), sorted.end(), [](const Proto& a, const Proto& b) { return a.out < b.out; });
+        auto last = [](const Proto& e) {
+            int lm = -1;
+            for (size_t j = 0; j < e.slot.size(); ++j) if (e.slot[j] >= 0) lm = (int)j;
+            return std::make_pair(lm, lm >= 0 ? e.slot[lm] : -1);
+        };
+        std::stable_sort(sorted.begin(), sorted.end(), [&](const Proto& a, const Proto& b) {
+            if (a.out != b.out) return a.out < b.out;
+            return last(a) < last(b);
+        });
         for (auto& e : sorted) {
             TtnEntry te{};
             te.wr = e.w.real(); te.wi = e.w.imag(); te.out = e.out;
@@ -881,9 +891,9 @@ std::string make_plan(const Tree& t, const Hamiltonian* h, int precision, Plan& 
     p.bond_off = off;
     off = align_up(off + (int64_t)max_chi * max_chi * 16, 256);
     p.work_off = off;
-    // (KMAX+1) Krylov vectors + 2 scratch tensors in the bulk type, then 2
+    // (KMAX+1) Krylov vectors + 3 scratch tensors in the bulk type, then 2
     // FP64 QR matrices
-    off = align_up(off + (int64_t)(TTN_KMAX + 3) * p.smax * (int64_t)p.esz + 2 * p.smax * 16, 256);
+    off = align_up(off + (int64_t)(TTN_KMAX + 4) * p.smax * (int64_t)p.esz + 2 * p.smax * 16, 256);
     p.status_off = off; off += 64;
     p.steps_off = off; off += 64;
     p.flops_off = off; off += 64;
