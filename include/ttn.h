@@ -174,6 +174,26 @@ ttn_status ttn_get_state(ttn_ctx* ctx, ttn_c128* tensors, int64_t* offsets);
 /* Bond dimension of every node to its parent (root: 1), out[n_nodes]. */
 ttn_status ttn_bond_dims(ttn_ctx* ctx, int* out);
 
+/* Effective-Hamiltonian action on one node tensor (paper Sec. II.C, Eq.
+ * psi_eom_1 without the factor -i), on caller-owned DEVICE buffers:
+ *     y = sum_t coeff[t] (x_j M_{t,j}) x,
+ * where M_{t,j} acts on index j of the row-major tensor x (dims[0..D-1],
+ * 1 <= D <= 8, every dims[j] <= 64) as y[.., p, ..] = sum_m M[p, m] x[.., m, ..].
+ *   factor[t*D + j]  index into mats of the dims[j] x dims[j] row-major
+ *                    complex128 matrix of term t on index j, or -1 (identity).
+ *   mats[i]          DEVICE pointer to matrix i (host array of n_mats pointers).
+ *   x, y             DEVICE pointers to prod(dims) complex128 values; y must
+ *                    not overlap x or any matrix.
+ * This is the contraction the sweep evaluates inside its Krylov
+ * exponentials, with environment matrices as the factors.  The call
+ * allocates its device scratch (three tensors and the term tables) with
+ * cudaMalloc, runs one thread block on `stream` (a cudaStream_t, NULL for
+ * the legacy default stream), waits for it, and frees the scratch.  Errors
+ * are reported through ttn_last_error(NULL). */
+ttn_status ttn_heff_apply(void* stream, int D, const int* dims, int n_terms, const ttn_c128* coeff,
+                          const int* factor, int n_mats, const void* const* mats, const ttn_c128* x,
+                          ttn_c128* y);
+
 /* Make `device` the CUDA device on which the calling thread's subsequent
  * ttn_create calls allocate (the library carries its own CUDA runtime, so
  * a device selected through another runtime, e.g. PyTorch's, is not seen). */

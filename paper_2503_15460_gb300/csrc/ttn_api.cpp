@@ -465,6 +465,81 @@ ttn_status ttn_bond_dims(ttn_ctx* c, int* out) {
     return TTN_OK;
 }
 
+namespace {
+
+// Validate a kernel-level operator and build its entry / slot tables.
+ttn_status build_heff_tables(int D, const int* dims, int n_terms, const ttn_c128* coeff, const int* factor,
+                             int n_mats, const void* const* mats, int64_t* S_out, std::vector<TtnEntry>& ents,
+                             std::vector<TtnSlot>& slots) {
+    if (D < 1 || D > TTN_MAXD || !dims || n_terms < 0 || (n_terms > 0 && (!coeff || !factor)) || n_mats < 0 ||
+        (n_mats > 0 && !mats))
+        return fail(nullptr, TTN_E_INVALID, "bad operator description");
+    int64_t S = 1;
+    for (int j = 0; j < D; ++j) {
+        if (dims[j] < 1 || dims[j] > TTN_MAXCHI) return fail(nullptr, TTN_E_INVALID, "dims out of range");
+        S *= dims[j];
+    }
+    slots.assign(std::max(1, n_mats), TtnSlot{nullptr, 0, 0});
+    for (int i = 0; i < n_mats; ++i) {
+        if (!mats[i]) return fail(nullptr, TTN_E_INVALID, "null matrix pointer");
+        slots[i].ptr = const_cast<void*>(mats[i]);
+    }
+    ents.clear();
+    for (int t = 0; t < n_terms; ++t) {
+        TtnEntry e{};
+        e.wr = coeff[t].re; e.wi = coeff[t].im; e.out = -1;
+        for (int j = 0; j < TTN_MAXD; ++j) e.slot[j] = -1;
+        for (int j = 0; j < D; ++j) {
+            int f = factor[t * D + j];
+            if (f < -1 || f >= n_mats) return fail(nullptr, TTN_E_INVALID, "factor index out of range");
+            e.slot[j] = f;
+            if (f >= 0) {
+                if (slots[f].rows && slots[f].rows != dims[j]) return fail(nullptr, TTN_E_INVALID, "matrix used on indices of different dimension");
+                slots[f].rows = slots[f].cols = dims[j];
+            }
+        }
+        ents.push_back(e);
+    }
+    // adjacent entries sharing their last factor are summed before it is applied
+    auto last = [D](const TtnEntry& e) {
+        int lm = -1;
+        for (int j = 0; j < D; ++j) if (e.slot[j] >= 0) lm = j;
+        return std::make_pair(lm, lm >= 0 ? e.slot[lm] : -1);
+    };
+    std::stable_sort(ents.begin(), ents.end(), [&](const TtnEntry& a, const TtnEntry& b) { return last(a) < last(b); });
+    *S_out = S;
+    return TTN_OK;
+}
+
+}  // namespace
+
+ttn_status ttn_heff_apply(void* stream, int D, const int* dims, int n_terms, const ttn_c128* coeff, const int* factor,
+                          int n_mats, const void* const* mats, const ttn_c128* x, ttn_c128* y) {
+    std::vector<TtnEntry> ents;
+    std::vector<TtnSlot> slots;
+    int64_t S = 0;
+    ttn_status st = build_heff_tables(D, dims, n_terms, coeff, factor, n_mats, mats, &S, ents, slots);
+    if (st) return st;
+    if (!x || !y) return fail(nullptr, TTN_E_INVALID, "null tensor pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    ttn_ctx* c = nullptr;   // errors of this call are reported through ttn_last_error(NULL)
+    const size_t tens = (size_t)S * 16;
+    const size_t eb = std::max<size_t>(1, ents.size()) * sizeof(TtnEntry), sb = slots.size() * sizeof(TtnSlot);
+    char* scratch = nullptr;
+    CK(cudaMalloc(&scratch, 3 * tens + eb + sb), "cudaMalloc (scratch)");
+    char* de = scratch + 3 * tens;
+    char* ds = de + eb;
+    cudaError_t e = cudaMemcpyAsync(de, ents.data(), ents.size() * sizeof(TtnEntry), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ds, slots.data(), sb, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = (cudaError_t)ttn_launch_heff((const TtnEntry*)de, (int)ents.size(), (const TtnSlot*)ds, D, dims, x, y,
+                                         scratch, scratch + tens, scratch + 2 * tens, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(scratch);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ttn_heff_apply");
+    return TTN_OK;
+}
+
 ttn_status ttn_set_device(int device) {
     cudaError_t e = cudaSetDevice(device);
     if (e != cudaSuccess) return fail(nullptr, TTN_E_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));

@@ -943,7 +943,33 @@ __global__ void __launch_bounds__(kThreads, 2) program_kernel(const TtnInstance*
         for (int i = 0; i < 8; ++i) atomicAdd(&in.op_cycles[16 + i], s_sub[i]);
 }
 
+// One thread block applies a sum-of-products operator to one tensor (the
+// same device routine the sweep runs inside its Krylov exponentials).
+__global__ void __launch_bounds__(kThreads, 1) heff_kernel(const TtnEntry* es, int ne, const TtnSlot* slots, int D,
+                                                           Shape sh, const double2* x, double2* y, double2* t1,
+                                                           double2* t2, double2* t3) {
+    if (threadIdx.x == 0) s_flops = 0.0;
+    __syncthreads();
+    (void)D;
+    heff_apply(y, x, t1, t2, t3, sh, es, ne, slots);
+}
+
 }  // namespace
+
+int ttn_launch_heff(const TtnEntry* d_entries, int ne, const TtnSlot* d_slots, int D, const int* dims,
+                    const void* x, void* y, void* t1, void* t2, void* t3, cudaStream_t s) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(heff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kStageBytes);
+        attr_set = true;
+    }
+    Shape sh;
+    sh.D = D;
+    for (int j = 0; j < TTN_MAXD; ++j) sh.d[j] = j < D ? dims[j] : 1;
+    heff_kernel<<<1, kThreads, kStageBytes, s>>>(d_entries, ne, d_slots, D, sh, (const double2*)x, (double2*)y,
+                                                 (double2*)t1, (double2*)t2, (double2*)t3);
+    return (int)cudaGetLastError();
+}
 
 int ttn_launch_program(int precision, const TtnInstance* d_insts, int n_inst, double dt, int nrep, cudaStream_t s) {
     if (n_inst <= 0) return 0;
