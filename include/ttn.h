@@ -194,6 +194,27 @@ ttn_status ttn_heff_apply(void* stream, int D, const int* dims, int n_terms, con
                           const int* factor, int n_mats, const void* const* mats, const ttn_c128* x,
                           ttn_c128* y);
 
+/* Allocation-free variant of ttn_heff_apply: same arguments, same result.
+ * The paper has no counterpart; this entry point exists for callers that
+ * must not allocate device memory during the call (for instance a serving
+ * loop whose device memory is owned by its own pool allocator, or code that
+ * cannot afford the device-wide synchronisation cudaMalloc/cudaFree may
+ * cause).  It calls no cudaMalloc, cudaFree or other allocating routine: its
+ * scratch (three tensors and the term tables, 1.6 MB) is a static array in
+ * device memory that every GPU loading the library holds until the process
+ * exits.  Limits: prod(dims) <= 32768 elements, n_terms <= 512,
+ * n_mats <= 512; larger requests return TTN_E_INVALID with a message.
+ * The first call on a device looks up the array's device address (with that
+ * device current) and caches it; make that first call before any stream
+ * capture.  All calls share the one array, and it keeps the contents of the
+ * last call: calls whose work can overlap on the GPU (several streams or
+ * host threads) race on it and must be serialised by the caller.  Runs one
+ * thread block on `stream` and waits for it; errors through
+ * ttn_last_error(NULL). */
+ttn_status ttn_heff_apply_noalloc(void* stream, int D, const int* dims, int n_terms, const ttn_c128* coeff,
+                                  const int* factor, int n_mats, const void* const* mats,
+                                  const ttn_c128* x, ttn_c128* y);
+
 /* Make `device` the CUDA device on which the calling thread's subsequent
  * ttn_create calls allocate (the library carries its own CUDA runtime, so
  * a device selected through another runtime, e.g. PyTorch's, is not seen). */

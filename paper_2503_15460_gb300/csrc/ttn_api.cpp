@@ -540,6 +540,30 @@ ttn_status ttn_heff_apply(void* stream, int D, const int* dims, int n_terms, con
     return TTN_OK;
 }
 
+ttn_status ttn_heff_apply_noalloc(void* stream, int D, const int* dims, int n_terms, const ttn_c128* coeff,
+                                  const int* factor, int n_mats, const void* const* mats, const ttn_c128* x,
+                                  ttn_c128* y) {
+    std::vector<TtnEntry> ents;
+    std::vector<TtnSlot> slots;
+    int64_t S = 0;
+    ttn_status st = build_heff_tables(D, dims, n_terms, coeff, factor, n_mats, mats, &S, ents, slots);
+    if (st) return st;
+    if (!x || !y) return fail(nullptr, TTN_E_INVALID, "null tensor pointer");
+    if (S > TTN_NOALLOC_MAX_ELEMS)
+        return fail(nullptr, TTN_E_INVALID, "tensor has " + std::to_string(S) + " elements; the allocation-free entry point takes at most " +
+                                                std::to_string(TTN_NOALLOC_MAX_ELEMS));
+    if (n_terms > TTN_NOALLOC_MAX_TERMS || n_mats > TTN_NOALLOC_MAX_MATS)
+        return fail(nullptr, TTN_E_INVALID, "at most " + std::to_string(TTN_NOALLOC_MAX_TERMS) + " terms and " +
+                                                std::to_string(TTN_NOALLOC_MAX_MATS) + " matrices in the allocation-free entry point");
+    cudaStream_t s = (cudaStream_t)stream;
+    ttn_ctx* c = nullptr;
+    cudaError_t e = (cudaError_t)ttn_launch_heff_noalloc(ents.data(), (int)ents.size(), slots.data(), (int)slots.size(),
+                                                         D, dims, x, y, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ttn_heff_apply_noalloc");
+    return TTN_OK;
+}
+
 ttn_status ttn_set_device(int device) {
     cudaError_t e = cudaSetDevice(device);
     if (e != cudaSuccess) return fail(nullptr, TTN_E_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));

@@ -13,6 +13,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "ttn_program.h"
 #include "ttn_launch.h"
 
@@ -982,4 +984,62 @@ int ttn_launch_program(int precision, const TtnInstance* d_insts, int n_inst, do
     if (precision == 0) program_kernel<double2, double2><<<n_inst, kThreads, kStageBytes, s>>>(d_insts, n_inst, dt, nrep);
     else program_kernel<double2, float2><<<n_inst, kThreads, kStageBytes, s>>>(d_insts, n_inst, dt, nrep);
     return (int)cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free effective-Hamiltonian application.
+//
+// Some callers must not allocate device memory while they run -- for example
+// a serving loop that has handed all of the GPU's memory to its own pool
+// allocator, or code that must not trigger the device-wide synchronisation
+// that cudaMalloc / cudaFree can imply.  For them the scratch of the
+// effective-Hamiltonian kernel (three tensors plus the term tables) lives in
+// one file-scope device array of fixed size instead of being allocated per
+// call.  Every GPU that loads the library keeps this array for the life of
+// the process.  All calls share it: calls whose work overlaps on the GPU
+// (different streams, different host threads) race on it and must be
+// serialised by the caller.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_heff_scratch[TTN_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_scratch_mutex;
+void* g_scratch_addr[64] = {nullptr};
+}  // namespace
+
+// Device address of the static scratch on the current device.  In host code
+// g_heff_scratch only names a host-side stand-in, so the address is looked
+// up once per device (with that device current) and cached.
+int ttn_noalloc_scratch(void** ptr) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return (int)e;
+    if (dev < 0 || dev >= 64) return (int)cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_addr[dev]) {
+        void* a = nullptr;
+        e = cudaGetSymbolAddress(&a, g_heff_scratch);
+        if (e != cudaSuccess) return (int)e;
+        g_scratch_addr[dev] = a;
+    }
+    *ptr = g_scratch_addr[dev];
+    return 0;
+}
+
+int ttn_launch_heff_noalloc(const TtnEntry* h_entries, int ne, const TtnSlot* h_slots, int n_slots, int D,
+                            const int* dims, const void* x, void* y, cudaStream_t s) {
+    void* base = nullptr;
+    int rc = ttn_noalloc_scratch(&base);
+    if (rc) return rc;
+    char* b = (char*)base;
+    // layout: [3 tensors][entries][slot table]
+    char* t1 = b;
+    char* t2 = t1 + TTN_NOALLOC_MAX_ELEMS * 16;
+    char* t3 = t2 + TTN_NOALLOC_MAX_ELEMS * 16;
+    char* de = t3 + TTN_NOALLOC_MAX_ELEMS * 16;
+    char* ds = de + TTN_NOALLOC_MAX_TERMS * sizeof(TtnEntry);
+    cudaError_t e = cudaMemcpyAsync(de, h_entries, (size_t)ne * sizeof(TtnEntry), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ds, h_slots, (size_t)n_slots * sizeof(TtnSlot), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return (int)e;
+    return ttn_launch_heff((const TtnEntry*)de, ne, (const TtnSlot*)ds, D, dims, x, y, t1, t2, t3, s);
 }

@@ -14,3 +14,16 @@ int ttn_launch_program(int precision, const TtnInstance* d_insts, int n_inst, do
 // tensors of prod(dims) complex128 elements each.  Returns a cudaError_t code.
 int ttn_launch_heff(const TtnEntry* d_entries, int ne, const TtnSlot* d_slots, int D, const int* dims,
                     const void* x, void* y, void* t1, void* t2, void* t3, cudaStream_t stream);
+
+// Limits of the allocation-free effective-Hamiltonian entry point: tensor
+// elements, terms and matrices, and the size of its static device scratch.
+#define TTN_NOALLOC_MAX_ELEMS 32768
+#define TTN_NOALLOC_MAX_TERMS 512
+#define TTN_NOALLOC_MAX_MATS 512
+#define TTN_NOALLOC_SCRATCH_BYTES \
+    (3 * TTN_NOALLOC_MAX_ELEMS * 16 + TTN_NOALLOC_MAX_TERMS * sizeof(TtnEntry) + TTN_NOALLOC_MAX_MATS * sizeof(TtnSlot))
+
+// Same as ttn_launch_heff with the scratch and the term tables in the static
+// device array (host tables are copied into it on `stream`).
+int ttn_launch_heff_noalloc(const TtnEntry* h_entries, int ne, const TtnSlot* h_slots, int n_slots, int D,
+                            const int* dims, const void* x, void* y, cudaStream_t stream);

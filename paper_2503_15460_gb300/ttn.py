@@ -53,6 +53,7 @@ _sig = {
     "ttn_set_stream": ([_P, _P], C.c_int),
     "ttn_set_device": ([C.c_int], C.c_int),
     "ttn_heff_apply": ([_P, C.c_int, _I32, C.c_int, _C128, _I32, C.c_int, C.POINTER(_P), _P, _P], C.c_int),
+    "ttn_heff_apply_noalloc": ([_P, C.c_int, _I32, C.c_int, _C128, _I32, C.c_int, C.POINTER(_P), _P, _P], C.c_int),
     "ttn_op_cycles": ([_P, np.ctypeslib.ndpointer(dtype=np.uint64, flags="C_CONTIGUOUS")], C.c_int),
     "ttn_step_stats": ([_P, C.POINTER(C.c_int64), C.POINTER(C.c_double),
                         np.ctypeslib.ndpointer(dtype=np.uint64, flags="C_CONTIGUOUS"), C.c_int,
@@ -217,6 +218,17 @@ def ttn_heff_apply(stream, dims, coeff, factor, mat_ptrs, x_ptr, y_ptr):
     mp = (_P * max(1, len(mat_ptrs)))(*[int(a) for a in mat_ptrs])
     _check(_lib.ttn_heff_apply(C.c_void_p(int(stream or 0)), len(dims), dims, len(coeff), coeff, factor,
                                len(mat_ptrs), mp, C.c_void_p(int(x_ptr)), C.c_void_p(int(y_ptr))), None)
+
+
+def ttn_heff_apply_noalloc(stream, dims, coeff, factor, mat_ptrs, x_ptr, y_ptr):
+    """Allocation-free ttn_heff_apply (static device scratch shared by all
+    calls; limits and the race between overlapping calls in include/ttn.h)."""
+    dims = np.ascontiguousarray(dims, dtype=np.int32)
+    coeff = np.ascontiguousarray(coeff, dtype=np.complex128)
+    factor = np.ascontiguousarray(factor, dtype=np.int32).reshape(-1)
+    mp = (_P * max(1, len(mat_ptrs)))(*[int(a) for a in mat_ptrs])
+    _check(_lib.ttn_heff_apply_noalloc(C.c_void_p(int(stream or 0)), len(dims), dims, len(coeff), coeff, factor,
+                                       len(mat_ptrs), mp, C.c_void_p(int(x_ptr)), C.c_void_p(int(y_ptr))), None)
 
 
 def ttn_set_device(device: int):
