@@ -41,6 +41,23 @@ N_SM = 152
 SM_MAX_MHZ = 2070.0
 
 
+def measured_traffic(batch):
+    """DRAM bytes of one launch (batch instance-steps) from the committed ncu
+    summary, if it was measured on the current kernel source; else None."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic_program_kernel_vibronic2x24_mixed.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    h = hashlib.sha256()
+    for f in ("ttn_kernels.cu", "ttn_program.h"):
+        h.update(open(os.path.join(ROOT, "paper_2503_15460_gb300", "csrc", f), "rb").read())
+    if h.hexdigest() != rec.get("kernel_source_sha256"):
+        return None
+    return rec["dram_bytes_per_instance_step"] * batch
+
+
 def workload_name(batch):
     return (f"vibronic 2 states x 24 modes, ML tree depth 4 (46 nodes, bonds 24/16/12/8, "
             f"local dims 10..30), batch of {batch} seeded instances, dt={DT}")
@@ -330,7 +347,7 @@ def main():
             "speedup_vs_fp64": (r["value"] / r["fp64"]["value"]) if r["fp64"] else None,
             "gpu_launches": args.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": measured_traffic(args.batch),
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz (no FP32 entry in the measured peaks)",
                          "flops_per_step": r["flops_per_step"]},
             "clocks": r["clocks"],
