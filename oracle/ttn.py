@@ -423,3 +423,133 @@ def full_state(tree, A):
     T = T[..., 0]
     T = np.transpose(T, perm)
     return T.reshape(-1)
+
+
+# ----------------------------------------------------------------------------
+# Subspace expansion (paper Sec. II.D): spawning of single-particle functions
+# ----------------------------------------------------------------------------
+class ExpandingTTN(TTN):
+    """TTN with bond-dimension expansion by the two-site energy variance.
+
+    With the orthogonality centre at z, the bond to child c = children(z)[k]
+    is expanded by the dominant left singular vectors u of
+        Y = (1 - P_c) G (1 - P_S),
+    where G[J, Theta] = <Phi^c_J (x) Theta| H |Psi> is the two-site projection
+    of H Psi onto c's children-product basis J and the orthonormal basis Theta
+    of everything outside c, P_c = A^c A^c^dag projects onto c's current SPFs
+    and P_S onto c's single-hole functions (the columns of the QR of A^z
+    along k); Y Y^dag is the operator Delta^(z,k) of Sec. II.D.  A vector is
+    added when dt * sqrt(lambda) >= eps (Sec. II.D spawning criterion with
+    c = dt), at most up to chi_max and the sizes of the two sides; the new
+    columns are appended to A^c and A^z is zero-padded along k, which leaves
+    Psi unchanged.  Dense "full approach" (Sec. III.B).
+
+    One expansion pass visits the bonds in sweep order (children in index
+    order, centre moved by QR); at the first bond that accepts vectors it
+    expands, moves the centre back to the root and starts over, until a
+    pass accepts nothing."""
+
+    def __init__(self, tree, H, A, **kw):
+        import copy
+        tree = copy.deepcopy(tree)
+        super().__init__(tree, H, A, **kw)
+        self.spawn_log = []
+
+    def two_site_action(self, z, k):
+        """Two-site tensor T = A^c x_last,k A^z and G = H_two-site T (plain SOP,
+        per-term environments).  Axes: c's child indices, then z's indices
+        without k (other children in order, then the parent)."""
+        c = self.ch[z][k]
+        Ac, Az = self.A[c], self.A[z]
+        nc = Ac.ndim - 1
+        T = np.tensordot(Ac, Az, axes=([nc], [k]))
+        zmodes = [j for j in range(Az.ndim) if j != k]
+        G = np.zeros_like(T)
+        for r, cr in enumerate(self.H.coeffs):
+            X = T
+            if self.t.is_leaf(c):
+                M = self.fac[r].get(c)
+                if M is not None:
+                    X = mode_product(M, X, 0)
+            else:
+                for j, cj in enumerate(self.ch[c]):
+                    if self.inside[cj, r]:
+                        X = mode_product(self.up[cj][r], X, j)
+            for pos, j in enumerate(zmodes):
+                ax = nc + pos
+                if j == Az.ndim - 1:
+                    if self.outside[z, r]:
+                        X = mode_product(self.down[z][r], X, ax)
+                else:
+                    cj = self.ch[z][j]
+                    if self.inside[cj, r]:
+                        X = mode_product(self.up[cj][r], X, ax)
+            G += cr * X
+        return T, G
+
+    def spawn_spf(self, z, k, dt, eps, chi_max):
+        c = self.ch[z][k]
+        chi = int(self.t.bond_dim[c])
+        _, G = self.two_site_action(z, k)
+        Ac = self.A[c]
+        NJ = int(np.prod(Ac.shape[:-1]))
+        NT = G.size // NJ
+        cap = min(chi_max, NJ, NT) - chi
+        if cap <= 0:
+            return 0
+        Gm = G.reshape(NJ, NT)
+        Mm = Ac.reshape(NJ, chi)
+        Qs, _ = qr_along(self.A[z], k, self.qr_tol)
+        Qm = np.moveaxis(Qs, k, -1).reshape(NT, chi)
+        Y = Gm - Mm @ (Mm.conj().T @ Gm)
+        Y = Y - (Y @ Qm.conj()) @ Qm.T
+        U, s, _ = np.linalg.svd(Y, full_matrices=False)
+        acc = [i for i in range(len(s)) if dt * s[i] >= eps][:cap]
+        self.spawn_log.append((z, k, s[: min(len(s), cap + 2)].copy()))
+        p = len(acc)
+        if p == 0:
+            return 0
+        newM = np.concatenate([Mm, U[:, acc]], axis=1)
+        self.A[c] = newM.reshape(Ac.shape[:-1] + (chi + p,))
+        Az = np.moveaxis(self.A[z], k, -1)
+        pad = np.zeros(Az.shape[:-1] + (p,), dtype=np.complex128)
+        self.A[z] = np.moveaxis(np.concatenate([Az, pad], axis=-1), -1, k)
+        self.t.bond_dim[c] = chi + p
+        self.build_up(c)
+        return p
+
+    def _visit(self, z, dt, eps, chi_max):
+        for k, c in enumerate(self.ch[z]):
+            p = self.spawn_spf(z, k, dt, eps, chi_max)
+            if p > 0:
+                return z, p
+            self._move_down(z, k)
+            hit = self._visit(c, dt, eps, chi_max)
+            if hit is not None:
+                return hit
+            C = self._move_up(z, k)
+            self.A[z] = mode_product(C, self.A[z], k)
+        return None
+
+    def _centre_to_root(self, z):
+        while z != 0:
+            p = int(self.t.parent[z])
+            k = self.ch[p].index(z)
+            C = self._move_up(p, k)
+            self.A[p] = mode_product(C, self.A[p], k)
+            z = p
+
+    def expand_pass(self, dt, eps, chi_max):
+        """Returns the number of functions added."""
+        added = 0
+        while True:
+            hit = self._visit(0, dt, eps, chi_max)
+            if hit is None:
+                return added
+            added += hit[1]
+            self._centre_to_root(hit[0])
+
+    def step_adaptive(self, dt, eps, chi_max, nsteps=1):
+        for _ in range(nsteps):
+            self.expand_pass(dt, eps, chi_max)
+            self.step(dt)
