@@ -68,11 +68,19 @@ typedef struct {
                             <= 0 selects 1e-13 (FP64) or 1e-10 (MIXED)           */
     int krylov_maxdim;   /* Krylov dimension before the interval is halved,
                             1..32; <= 0 selects 32                               */
-    double eps_spawn;    /* subspace-expansion tolerance (Sec. II.D); unused
-                            while expand == 0                                    */
-    int chi_max;         /* bond-dimension cap for expansion; unused while
-                            expand == 0                                          */
-    int expand;          /* 0: fixed bond dimensions                              */
+    double eps_spawn;    /* subspace-expansion tolerance eps_S (Sec. II.D): a
+                            new single-particle function is added when
+                            dt * sqrt(lambda) >= eps_spawn                       */
+    int chi_max;         /* bond-dimension cap for expansion (<= 64)             */
+    int expand;          /* 0: fixed bond dimensions; 1: before every step, an
+                            expansion pass visits the bonds in sweep order with
+                            the orthogonality centre on the bond's parent and
+                            adds to the child the dominant eigenvectors of the
+                            two-site energy-variance operator (1-P) G (1-P_S)
+                            that pass the criterion (at most 16 per bond and
+                            growth); after each growth the centre returns to
+                            the root and the pass restarts, until a pass adds
+                            nothing.  ttn_bond_dims reports the result.          */
     double qr_rank_tol;  /* a QR column whose remainder has norm <= qr_rank_tol
                             * ||M||_F is treated as zero and completed by the
                             deterministic unit vector (unoccupied function);
@@ -145,7 +153,8 @@ ttn_status ttn_step(ttn_ctx* ctx, double dt, int nsteps, const ttn_step_opts* op
 
 /* Advance n independent contexts (same precision) by nsteps steps of dt in
  * one device launch, one thread block per context; the stream of ctxs[0]
- * is used.  Contexts may have different trees and Hamiltonians. */
+ * is used.  Contexts may have different trees and Hamiltonians.  Fixed bond
+ * dimensions only (opts->expand must be 0). */
 ttn_status ttn_step_batch(ttn_ctx* const* ctxs, int n, double dt, int nsteps,
                           const ttn_step_opts* opts);
 

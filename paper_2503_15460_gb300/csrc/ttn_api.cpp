@@ -42,14 +42,16 @@ struct ttn_ctx {
     size_t ops_bytes = 0;
     TtnSlot* d_slots = nullptr;
     TtnEntry* d_entries = nullptr;
-    DevProgram init_p, step_p, ne_p;
-    std::vector<DevProgram> rdm_p, vac_p;
+    DevProgram init_p, step_p, ne_p, spawn_p;
+    std::vector<DevProgram> rdm_p, vac_p, to_root_p;
     TtnInstance* d_inst = nullptr; // staging for single-instance launches
     TtnInstance* d_batch = nullptr;
     int batch_cap = 0;
     double ktol = 0.0;
     double qtol = 0.0;
     int kmax = TTN_KMAX;
+    int64_t steps_total = 0;
+    int64_t spawned = 0;            // single-particle functions added by expansion
 };
 
 namespace {
@@ -109,6 +111,9 @@ TtnInstance make_instance(ttn_ctx* c, const DevProgram& p) {
     in.ktol = c->ktol > 0 ? c->ktol : (c->precision == TTN_MIXED ? 1e-10 : 1e-13);
     in.qtol = c->qtol > 0 ? c->qtol : 1e-10;
     in.kmax = c->kmax;
+    in.spawn_out = (double*)(c->d_state + c->plan.spawn_out_off);
+    in.spawn_ws = c->d_state + c->plan.spawn_ws_off;
+    in.spawn_kmax = c->plan.spawn_kmax;
     return in;
 }
 
@@ -131,14 +136,25 @@ ttn_status run_program(ttn_ctx* c, const DevProgram& p, double dt, int nrep) {
     return check_status(c);
 }
 
+ttn_status check_status_spawn(ttn_ctx* c, bool* hit) {
+    int st = 0;
+    CK(cudaMemcpyAsync(&st, c->d_state + c->plan.status_off, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "status copy");
+    CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+    *hit = st == TTN_STATUS_SPAWN_HIT;
+    if (*hit) return TTN_OK;
+    if (st == 4) return fail(c, TTN_E_NOCONV, "Krylov exponential did not converge");
+    if (st != 0) return fail(c, TTN_E_CUDA, "device reported status " + std::to_string(st));
+    return TTN_OK;
+}
+
 void free_ops(ttn_ctx* c) {
     if (c->d_ops) cudaFree(c->d_ops);
     c->d_ops = nullptr;
     c->ops_bytes = 0;
     c->d_slots = nullptr;
     c->d_entries = nullptr;
-    c->init_p = c->step_p = c->ne_p = DevProgram();
-    c->rdm_p.clear(); c->vac_p.clear();
+    c->init_p = c->step_p = c->ne_p = c->spawn_p = DevProgram();
+    c->rdm_p.clear(); c->vac_p.clear(); c->to_root_p.clear();
     c->d_inst = nullptr;
 }
 
@@ -149,9 +165,10 @@ ttn_status upload_ops(ttn_ctx* c) {
     size_t slot_bytes = 0;
     for (auto& s : P.slots) slot_bytes = std::max(slot_bytes, (size_t)s.off + (size_t)s.rows * s.cols * P.esz);
     slot_bytes = al(slot_bytes);
-    std::vector<const ttn::Program*> progs{&P.init_prog, &P.step_prog, &P.norm_energy_prog};
+    std::vector<const ttn::Program*> progs{&P.init_prog, &P.step_prog, &P.norm_energy_prog, &P.spawn_prog};
     for (auto& p : P.rdm_prog) progs.push_back(&p);
     for (auto& p : P.vac_prog) progs.push_back(&p);
+    for (auto& p : P.to_root_prog) progs.push_back(&p);
     size_t n_ops_total = 0;
     for (auto* p : progs) n_ops_total += p->ops.size();
     size_t off_table = slot_bytes;
@@ -189,6 +206,7 @@ ttn_status upload_ops(ttn_ctx* c) {
             o.a = s.a_off >= 0 ? (void*)(c->d_state + s.a_off) : nullptr;
             o.b = s.b_off >= 0 ? (void*)(c->d_state + s.b_off) : nullptr;
             o.out = s.out_off >= 0 ? (double*)(c->d_state + s.out_off) : nullptr;
+            if (o.type == TTN_OP_SPAWN) o.c = o.b;      // the child tensor
             std::memcpy(host.data() + cur, &o, sizeof(TtnOp));
             cur += sizeof(TtnOp);
         }
@@ -197,14 +215,109 @@ ttn_status upload_ops(ttn_ctx* c) {
     c->init_p = link(P.init_prog);
     c->step_p = link(P.step_prog);
     c->ne_p = link(P.norm_energy_prog);
+    c->spawn_p = link(P.spawn_prog);
     for (auto& p : P.rdm_prog) c->rdm_p.push_back(link(p));
     for (auto& p : P.vac_prog) c->vac_p.push_back(link(p));
+    for (auto& p : P.to_root_prog) c->to_root_p.push_back(link(p));
     c->d_slots = (TtnSlot*)(c->d_ops + off_table);
     c->d_entries = (TtnEntry*)(c->d_ops + off_entries);
     c->d_inst = (TtnInstance*)(c->d_ops + off_inst);
     CK(cudaMemcpyAsync(c->d_ops, host.data(), total, cudaMemcpyHostToDevice, c->stream), "operator upload");
     CK(cudaStreamSynchronize(c->stream), "stream synchronize");
     return TTN_OK;
+}
+
+ttn_status upload_state(ttn_ctx* c, const std::vector<std::vector<cplx>>& A);
+
+// Grow the bond of `child` by the p functions in U (NJ x p, column j of the
+// new block = U[j*NJ ..]): append them to the child's tensor, zero-pad the
+// parent's index, and rebuild plan, arenas, centre position and
+// environments for the new bond dimensions (paper Sec. II.D: the state is
+// unchanged by the padding).
+ttn_status grow_bond(ttn_ctx* c, int child, int p, const std::vector<cplx>& U) {
+    ttn::Tree& t = c->tree;
+    const int z = t.parent[child];
+    const int k = (int)(std::find(t.ch[z].begin(), t.ch[z].end(), child) - t.ch[z].begin());
+    std::vector<char> raw(c->plan.bond_off);
+    CK(cudaMemcpyAsync(raw.data(), c->d_state, raw.size(), cudaMemcpyDeviceToHost, c->stream), "state copy");
+    CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+    std::vector<std::vector<cplx>> A(t.n);
+    for (int u = 0; u < t.n; ++u) {
+        const cplx* src = (const cplx*)(raw.data() + c->plan.tensor_off[u]);
+        A[u].assign(src, src + t.size[u]);
+    }
+    const int chi = t.bond[child];
+    const int64_t NJ = t.size[child] / chi;
+    // child: [NJ x chi] -> [NJ x (chi + p)]
+    std::vector<cplx> Ac(NJ * (chi + p));
+    for (int64_t J = 0; J < NJ; ++J) {
+        for (int n = 0; n < chi; ++n) Ac[J * (chi + p) + n] = A[child][J * chi + n];
+        for (int j = 0; j < p; ++j) Ac[J * (chi + p) + chi + j] = U[(size_t)j * NJ + J];
+    }
+    // parent: index k grows from chi to chi + p with zeros
+    const auto& dz = t.dims[z];
+    int64_t Lk = 1, Rk = 1;
+    for (int j = 0; j < k; ++j) Lk *= dz[j];
+    for (size_t j = k + 1; j < dz.size(); ++j) Rk *= dz[j];
+    std::vector<cplx> Az(Lk * (chi + p) * Rk, 0.0);
+    for (int64_t l = 0; l < Lk; ++l)
+        for (int n = 0; n < chi; ++n)
+            for (int64_t r = 0; r < Rk; ++r) Az[(l * (chi + p) + n) * Rk + r] = A[z][(l * chi + n) * Rk + r];
+    A[child].swap(Ac);
+    A[z].swap(Az);
+    std::vector<int> bond = t.bond;
+    bond[child] = chi + p;
+    ttn::Tree nt;
+    std::string msg = ttn::build_tree(t.n, t.parent.data(), t.phys.data(), bond.data(), nt);
+    if (!msg.empty()) return fail(c, TTN_E_STATE, "bond growth produced an invalid tree: " + msg);
+    ttn::Plan P;
+    msg = ttn::make_plan(nt, &c->ham, c->precision, P);
+    if (!msg.empty()) return fail(c, TTN_E_STATE, msg);
+    char* fresh = nullptr;
+    CK(cudaMalloc(&fresh, P.total_bytes), "cudaMalloc (state)");
+    cudaFree(c->d_state);
+    c->d_state = fresh;
+    c->state_bytes = P.total_bytes;
+    CK(cudaMemsetAsync(c->d_state, 0, c->state_bytes, c->stream), "memset");
+    c->tree = nt;
+    c->plan = P;
+    ttn_status s = upload_ops(c);
+    if (s) { c->failed = true; return s; }
+    s = upload_state(c, A);
+    if (s) return s;
+    if (z > 0) { s = run_program(c, c->to_root_p[z], 0.0, 1); if (s) return s; }
+    return run_program(c, c->init_p, 0.0, 1);
+}
+
+// One expansion pass: run the spawn program until it finishes without a hit.
+ttn_status expand_pass(ttn_ctx* c, double dt, double eps, int chi_max) {
+    for (int guard = 0; guard < 100000; ++guard) {
+        if (c->spawn_p.n_ops == 0) return TTN_OK;
+        TtnInstance in = make_instance(c, c->spawn_p);
+        in.chi_max = chi_max; in.spawn_eps = eps; in.spawn_dt = dt;
+        CK(cudaMemcpyAsync(c->d_inst, &in, sizeof(in), cudaMemcpyHostToDevice, c->stream), "instance upload");
+        int e = ttn_launch_program(c->precision, c->d_inst, 1, dt, 1, c->stream);
+        if (e != 0) return cuda_fail(c, (cudaError_t)e, "kernel launch");
+        bool hit = false;
+        ttn_status s = check_status_spawn(c, &hit);
+        if (s) return s;
+        if (!hit) return TTN_OK;
+        double hdr[4];
+        CK(cudaMemcpyAsync(hdr, c->d_state + c->plan.spawn_out_off, sizeof(hdr), cudaMemcpyDeviceToHost, c->stream), "spawn copy");
+        CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+        const int child = (int)hdr[1], p = (int)hdr[2];
+        const int64_t NJ = (int64_t)hdr[3];
+        std::vector<cplx> U((size_t)NJ * p);
+        CK(cudaMemcpyAsync(U.data(), c->d_state + c->plan.spawn_out_off + 8 * (4 + TTN_SPAWN_MAX_NEW), U.size() * 16,
+                           cudaMemcpyDeviceToHost, c->stream), "spawn copy");
+        int zero = 0;
+        CK(cudaMemcpyAsync(c->d_state + c->plan.status_off, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream), "status reset");
+        CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+        s = grow_bond(c, child, p, U);
+        if (s) return s;
+        c->spawned += p;
+    }
+    return fail(c, TTN_E_STATE, "expansion pass did not terminate");
 }
 
 ttn_status upload_state(ttn_ctx* c, const std::vector<std::vector<cplx>>& A) {
@@ -316,6 +429,16 @@ ttn_status ttn_set_sop_hamiltonian(ttn_ctx* c, int n_terms, const ttn_c128* coef
     c->ham = h;
     c->has_h = true;
     c->plan = P;
+    if ((size_t)P.total_bytes > c->state_bytes) {
+        char* fresh = nullptr;
+        CK(cudaMalloc(&fresh, P.total_bytes), "cudaMalloc (state)");
+        CK(cudaMemsetAsync(fresh, 0, P.total_bytes, c->stream), "memset");
+        CK(cudaMemcpyAsync(fresh, c->d_state, P.bond_off, cudaMemcpyDeviceToDevice, c->stream), "state copy");
+        CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+        cudaFree(c->d_state);
+        c->d_state = fresh;
+        c->state_bytes = P.total_bytes;
+    }
     ttn_status s = upload_ops(c);
     if (s) { c->failed = true; return s; }
     return run_program(c, c->init_p, 0.0, 1);
@@ -326,13 +449,21 @@ ttn_status ttn_step(ttn_ctx* c, double dt, int nsteps, const ttn_step_opts* opts
     if (!c->has_h) return fail(c, TTN_E_STATE, "no Hamiltonian set");
     if (nsteps < 0 || !std::isfinite(dt)) return fail(c, TTN_E_INVALID, "bad dt / nsteps");
     if (opts) {
-        if (opts->expand) return fail(c, TTN_E_INVALID, "subspace expansion is not enabled in this build");
         if (opts->krylov_maxdim > TTN_KMAX) return fail(c, TTN_E_INVALID, "krylov_maxdim must be <= 32");
+        if (opts->expand && (!(opts->eps_spawn > 0.0) || opts->chi_max < 1 || opts->chi_max > TTN_MAXCHI))
+            return fail(c, TTN_E_INVALID, "expansion needs eps_spawn > 0 and 1 <= chi_max <= 64");
         c->ktol = opts->krylov_tol;
         c->qtol = opts->qr_rank_tol;
         c->kmax = opts->krylov_maxdim > 0 ? opts->krylov_maxdim : TTN_KMAX;
     }
-    return run_program(c, c->step_p, dt, nsteps);
+    if (!opts || !opts->expand) return run_program(c, c->step_p, dt, nsteps);
+    for (int i = 0; i < nsteps; ++i) {
+        ttn_status s = expand_pass(c, dt, opts->eps_spawn, opts->chi_max);
+        if (s) return s;
+        s = run_program(c, c->step_p, dt, 1);
+        if (s) return s;
+    }
+    return TTN_OK;
 }
 
 ttn_status ttn_step_batch(ttn_ctx* const* ctxs, int n, double dt, int nsteps, const ttn_step_opts* opts) {
@@ -343,7 +474,7 @@ ttn_status ttn_step_batch(ttn_ctx* const* ctxs, int n, double dt, int nsteps, co
         if (!ctxs[i]->has_h) return fail(ctxs[i], TTN_E_STATE, "no Hamiltonian set");
         if (ctxs[i]->precision != c->precision) return fail(c, TTN_E_INVALID, "mixed precisions in one batch");
         if (opts) {
-            if (opts->expand) return fail(c, TTN_E_INVALID, "subspace expansion is not enabled in this build");
+            if (opts->expand) return fail(c, TTN_E_INVALID, "subspace expansion is run per context: use ttn_step");
             ctxs[i]->ktol = opts->krylov_tol;
             ctxs[i]->qtol = opts->qr_rank_tol;
             ctxs[i]->kmax = opts->krylov_maxdim > 0 ? std::min(opts->krylov_maxdim, TTN_KMAX) : TTN_KMAX;

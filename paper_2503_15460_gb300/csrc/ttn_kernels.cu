@@ -14,6 +14,9 @@
 #include <stdint.h>
 
 #include <mutex>
+#ifdef TTN_SPAWN_DEBUG
+#include <cstdio>
+#endif
 
 #include "ttn_program.h"
 #include "ttn_launch.h"
@@ -789,6 +792,374 @@ __device__ const TB* as_bulk(const TS* a, TB* buf, int64_t n) {
     return buf;
 }
 
+
+// ---------------------------------------------------------------------------
+// Subspace expansion (paper Sec. II.D).
+// ---------------------------------------------------------------------------
+// Hermitian eigen-decomposition A = V diag(A') V^H of an n x n complex matrix
+// (FP64, row-major, in place: the diagonal of A holds the eigenvalues on
+// return) by the cyclic Jacobi method with the parallel round-robin pair
+// ordering: in each round n/2 disjoint (p, q) pairs are rotated at once.
+// Each rotation is G = diag(1, e^{-i phi}) times the real rotation that
+// annihilates the now real off-diagonal element (Golub & Van Loan, Sec. 8.5).
+__device__ void jacobi_eigh(double2* A, double2* Vm, int n, Smem& sm) {
+    const int tid = threadIdx.x;
+    for (int i = tid; i < n * n; i += kThreads) Vm[i] = make_double2(i / n == i % n ? 1.0 : 0.0, 0.0);
+    const int nn = (n + 1) & ~1;
+    const int npair = nn / 2;
+    double* rc = (double*)dyn_smem;
+    double* rs = rc + npair;
+    double2* ph = (double2*)(rs + npair);
+    int* pp = (int*)(ph + npair);
+    int* pq = pp + npair;
+    __syncthreads();
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double2 part = make_double2(0.0, 0.0);
+        for (int i = tid; i < n * n; i += kThreads) {
+            const int r = i / n, c = i - r * n;
+            if (r != c) part.x += cabs2(A[i]);
+            else part.y += A[i].x * A[i].x;
+        }
+        const double2 nrm = block_sum(part, sm);
+        if (nrm.x <= 1e-30 * (nrm.x + nrm.y) || nrm.x == 0.0) break;
+        for (int rnd = 0; rnd < nn - 1; ++rnd) {
+            for (int i = tid; i < npair; i += kThreads) {
+                const int a = (i == 0) ? 0 : ((i - 1 + rnd) % (nn - 1)) + 1;
+                const int jj = nn - 1 - i;
+                const int b = ((jj - 1 + rnd) % (nn - 1)) + 1;
+                const int p = min(a, b), q = max(a, b);
+                double c = 1.0, sn = 0.0;
+                double2 e = make_double2(1.0, 0.0);
+                if (q < n) {
+                    const double2 apq = A[p * n + q];
+                    const double r = sqrt(cabs2(apq));
+                    if (r > 1e-300) {
+                        const double theta = (A[q * n + q].x - A[p * n + p].x) / (2.0 * r);
+                        const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                        c = 1.0 / sqrt(t * t + 1.0);
+                        sn = t * c;
+                        e = make_double2(apq.x / r, -apq.y / r);          // e^{-i phi}
+                    }
+                }
+                rc[i] = c; rs[i] = sn; ph[i] = e; pp[i] = p; pq[i] = q;
+            }
+            __syncthreads();
+            for (int idx = tid; idx < npair * n; idx += kThreads) {      // columns of A and V
+                const int i = idx / n, row = idx - (idx / n) * n;
+                const int p = pp[i], q = pq[i];
+                if (q >= n || rs[i] == 0.0) continue;
+                const double c = rc[i], sn = rs[i];
+                const double2 e = ph[i];
+                double2 ap = A[row * n + p], aq = cmul(e, A[row * n + q]);
+                A[row * n + p] = make_double2(c * ap.x - sn * aq.x, c * ap.y - sn * aq.y);
+                A[row * n + q] = make_double2(sn * ap.x + c * aq.x, sn * ap.y + c * aq.y);
+                ap = Vm[row * n + p]; aq = cmul(e, Vm[row * n + q]);
+                Vm[row * n + p] = make_double2(c * ap.x - sn * aq.x, c * ap.y - sn * aq.y);
+                Vm[row * n + q] = make_double2(sn * ap.x + c * aq.x, sn * ap.y + c * aq.y);
+            }
+            __syncthreads();
+            for (int idx = tid; idx < npair * n; idx += kThreads) {      // rows of A
+                const int i = idx / n, col = idx - (idx / n) * n;
+                const int p = pp[i], q = pq[i];
+                if (q >= n || rs[i] == 0.0) continue;
+                const double c = rc[i], sn = rs[i];
+                const double2 ec = make_double2(ph[i].x, -ph[i].y);     // e^{+i phi}
+                const double2 ap = A[p * n + col], aq = cmul(ec, A[q * n + col]);
+                A[p * n + col] = make_double2(c * ap.x - sn * aq.x, c * ap.y - sn * aq.y);
+                A[q * n + col] = make_double2(sn * ap.x + c * aq.x, sn * ap.y + c * aq.y);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// C = op(A) * B for small dense FP64 matrices (row-major): A is m x k (or
+// k x m when adjA, then conjugate-transposed), B is k x n.
+__device__ void small_gemm(double2* C, const double2* A, const double2* B, int m, int k, int n, bool adjA) {
+    for (int idx = threadIdx.x; idx < m * n; idx += kThreads) {
+        const int i = idx / n, j = idx - (idx / n) * n;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int l = 0; l < k; ++l) {
+            const double2 a = adjA ? make_double2(A[l * m + i].x, -A[l * m + i].y) : A[i * k + l];
+            acc = cadd(acc, cmul(a, B[l * n + j]));
+        }
+        C[idx] = acc;
+    }
+    count_flops(8.0 * m * k * n);
+    __syncthreads();
+}
+
+// Test the bond to child c = children(z)[k] for new single-particle
+// functions (the centre is at z).  With X_a the child's up channel a applied
+// at the two-site level to A^c, W~_a = sum_b w_ab D_b A^z the matching down
+// channels applied to A^z, P_c = A^c A^c^dag and P_S the projector on the
+// child's single-hole functions (QR of A^z along k),
+//     Y = (1 - P_c) G (1 - P_S) = X' W'^T,  Y Y^dag = X' C X'^dag,
+// with X' = (1 - P_c) X, W' = (1 - Q_S Q_S^dag) W~, C = W'^T conj W'.  The
+// dominant eigenvectors of Y Y^dag are found in span X': with
+// E = X'^dag X' = V L V^dag and F = V L^{-1/2} (numerically nonzero part),
+// T = F^dag E C E F is Hermitian and its eigenvector w gives u = X' F w.
+template <class TS, class TB>
+__device__ void spawn_op(const TtnOp& op, const TtnInstance& in, Smem& sm, TB* V, int64_t smax, TB* t1, TB* t2,
+                         double2* Wc, double2* Qc) {
+    Shape shz, shc;
+    shz.D = op.D; shc.D = op.Dc;
+    for (int j = 0; j < TTN_MAXD; ++j) {
+        shz.d[j] = j < op.D ? op.dims[j] : 1;
+        shc.d[j] = j < op.Dc ? op.dimsc[j] : 1;
+    }
+    const int k = op.k;
+    const int chi = shz.d[k];
+    const int64_t Sz = shz.size(), Sc = shc.size();
+    const int NJ = (int)(Sc / chi), NT = (int)(Sz / chi);
+    int cap = min(in.chi_max, min(NJ, NT)) - chi;
+    if (cap <= 0 || in.spawn_eps <= 0.0) return;
+    if (cap > TTN_SPAWN_MAX_NEW) cap = TTN_SPAWN_MAX_NEW;
+    // distinct non-identity up channels among the bond terms
+    const TtnEntry* eb = in.entries + op.e2;
+    int ids[13];
+    int A = 0;
+    for (int i = 0; i < op.ne2; ++i) {
+        const int a = eb[i].slot[0];
+        if (a < 0) continue;
+        bool seen = false;
+        for (int q = 0; q < A; ++q) seen |= ids[q] == a;
+        if (!seen) {
+            if (A == 13) return;                 // too many channels for the workspace
+            ids[A++] = a;
+        }
+    }
+    const int K = A * chi;
+    if (A == 0 || K > in.spawn_kmax) return;
+    const TtnSlot* slots = in.slots;
+    TB* Mc = V;
+    TB* Mz = V + smax;
+    TB* X = V + 2 * smax;                       // A buffers of Sc
+    TB* Wt = V + (2 + A) * smax;                // A buffers of Sz
+    TB* Wb = V + (2 + 2 * A) * smax;
+    TB* Qsc = V + (3 + 2 * A) * smax;
+    TB* g = V + (4 + 2 * A) * smax;             // chi x chi scratch
+    double2* ws = (double2*)in.spawn_ws;
+    double2* Acopy = ws;
+    double2* E = ws + smax;
+    double2* Cm = E + (int64_t)K * K;
+    double2* T = Cm + (int64_t)K * K;
+    double2* VE = T + (int64_t)K * K;
+    double2* WT = VE + (int64_t)K * K;
+    double2* P1 = WT + (int64_t)K * K;
+    {
+        const TS* Ac = (const TS*)op.c;
+        const TS* Az = (const TS*)op.a;
+        for (int64_t i = threadIdx.x; i < Sc; i += kThreads) Mc[i] = cT<TB>(cd(Ac[i]));
+        for (int64_t i = threadIdx.x; i < Sz; i += kThreads) { Mz[i] = cT<TB>(cd(Az[i])); Acopy[i] = cd(Az[i]); }
+        __syncthreads();
+    }
+    const int lastc = shc.D - 1;
+    // X_a = (1 - Mc Mc^dag) U_a Mc
+    for (int a = 0; a < A; ++a) {
+        TB* Xa = X + a * smax;
+        for (int64_t i = threadIdx.x; i < Sc; i += kThreads) Xa[i] = czero<TB>();
+        __syncthreads();
+        const TtnEntry* eu = in.entries + op.e0;
+        for (int i = 0; i < op.ne; ++i) {
+            const TtnEntry e = eu[i];
+            if (e.out != ids[a]) continue;
+            bool any = false;
+            for (int m = 0; m < shc.D; ++m) any |= (m != lastc && e.slot[m] >= 0);
+            if (!any) {
+                const TB wt = cT<TB>(make_double2(e.wr, e.wi));
+                for (int64_t x = threadIdx.x; x < Sc; x += kThreads) { TB o = Xa[x]; cfma(o, wt, Mc[x]); Xa[x] = o; }
+                __syncthreads();
+            } else {
+                apply_chain((const TB*)Mc, t1, t2, shc, e, slots, lastc, Xa, make_double2(e.wr, e.wi));
+            }
+        }
+        for (int i = threadIdx.x; i < chi * chi; i += kThreads) g[i] = czero<TB>();
+        __syncthreads();
+        gram_acc(g, (const TB*)Mc, (const TB*)Xa, shc, lastc, make_double2(1.0, 0.0));
+        mode_prod(Xa, (const TB*)Mc, shc.before(lastc), chi, chi, (int64_t)1, (const TB*)g, true,
+                  make_double2(-1.0, 0.0), true);
+        __syncthreads();
+    }
+    // W~_a = sum_b w_ab D_b Mz
+    for (int a = 0; a < A; ++a) {
+        TB* Wa = Wt + a * smax;
+        for (int64_t i = threadIdx.x; i < Sz; i += kThreads) Wa[i] = czero<TB>();
+        __syncthreads();
+        for (int i = 0; i < op.ne2; ++i) {
+            const TtnEntry tb = eb[i];
+            if (tb.slot[0] != ids[a]) continue;
+            const int bsl = tb.slot[1];
+            const TB* src = Mz;
+            if (bsl >= 0) {
+                for (int64_t x = threadIdx.x; x < Sz; x += kThreads) Wb[x] = czero<TB>();
+                __syncthreads();
+                const TtnEntry* ed = in.entries + op.e1;
+                for (int q = 0; q < op.ne1; ++q) {
+                    const TtnEntry e = ed[q];
+                    if (e.out != bsl) continue;
+                    bool any = false;
+                    for (int m = 0; m < shz.D; ++m) any |= (m != k && e.slot[m] >= 0);
+                    if (!any) {
+                        const TB wt = cT<TB>(make_double2(e.wr, e.wi));
+                        for (int64_t x = threadIdx.x; x < Sz; x += kThreads) { TB o = Wb[x]; cfma(o, wt, Mz[x]); Wb[x] = o; }
+                        __syncthreads();
+                    } else {
+                        apply_chain((const TB*)Mz, t1, t2, shz, e, slots, k, Wb, make_double2(e.wr, e.wi));
+                    }
+                }
+                src = Wb;
+            }
+            const TB wt = cT<TB>(make_double2(tb.wr, tb.wi));
+            for (int64_t x = threadIdx.x; x < Sz; x += kThreads) { TB o = Wa[x]; cfma(o, wt, src[x]); Wa[x] = o; }
+            __syncthreads();
+        }
+    }
+    // single-hole functions: Q of A^z along k (FP64)
+    qr_mode(Acopy, shz, k, Wc, Qc, in.qtol, sm);
+    for (int64_t i = threadIdx.x; i < Sz; i += kThreads) Qsc[i] = cT<TB>(Acopy[i]);
+    __syncthreads();
+    // W'_a = (1 - Qs Qs^dag) W~_a   (G (1 - P_S) = X (W'^T) with P_S acting on rows of G)
+    for (int a = 0; a < A; ++a) {
+        TB* Wa = Wt + a * smax;
+        for (int i = threadIdx.x; i < chi * chi; i += kThreads) g[i] = czero<TB>();
+        __syncthreads();
+        gram_acc(g, (const TB*)Qsc, (const TB*)Wa, shz, k, make_double2(1.0, 0.0));
+        mode_prod(Wa, (const TB*)Qsc, shz.before(k), chi, chi, shz.after(k), (const TB*)g, true,
+                  make_double2(-1.0, 0.0), true);
+        __syncthreads();
+    }
+    // E = X'^dag X', C = conj(W'^dag W')   (K x K, FP64)
+    for (int a = 0; a < A; ++a)
+        for (int b = 0; b < A; ++b) {
+            for (int i = threadIdx.x; i < chi * chi; i += kThreads) g[i] = czero<TB>();
+            __syncthreads();
+            gram_acc(g, (const TB*)(X + a * smax), (const TB*)(X + b * smax), shc, lastc, make_double2(1.0, 0.0));
+            for (int i = threadIdx.x; i < chi * chi; i += kThreads)
+                E[(int64_t)(a * chi + i / chi) * K + b * chi + i % chi] = cd(g[i]);
+            __syncthreads();
+            for (int i = threadIdx.x; i < chi * chi; i += kThreads) g[i] = czero<TB>();
+            __syncthreads();
+            gram_acc(g, (const TB*)(Wt + a * smax), (const TB*)(Wt + b * smax), shz, k, make_double2(1.0, 0.0));
+            for (int i = threadIdx.x; i < chi * chi; i += kThreads) {
+                const double2 v = cd(g[i]);
+                Cm[(int64_t)(a * chi + i / chi) * K + b * chi + i % chi] = make_double2(v.x, -v.y);
+            }
+            __syncthreads();
+        }
+    // trace(Y Y^dag) = trace(C E) bounds every eigenvalue
+    const double thr = (in.spawn_eps / in.spawn_dt) * (in.spawn_eps / in.spawn_dt);
+    {
+        double2 part = make_double2(0.0, 0.0);
+        for (int64_t idx = threadIdx.x; idx < (int64_t)K * K; idx += kThreads) {
+            const int i = (int)(idx / K), j = (int)(idx % K);
+            part = cadd(part, cmul(Cm[(int64_t)i * K + j], E[(int64_t)j * K + i]));
+        }
+        const double tr = block_sum(part, sm).x;
+#ifdef TTN_SPAWN_DEBUG
+        if (threadIdx.x == 0) printf("spawn z=%d c=%d A=%d K=%d NJ=%d NT=%d trace=%.3e thr=%.3e\n", op.node, op.child, A, K, NJ, NT, tr, thr);
+#endif
+        if (!(tr >= thr)) return;
+    }
+    // E = V L V^dag; F = V L^{-1/2} on the numerically nonzero part (stored in P1, K x r)
+    for (int64_t i = threadIdx.x; i < (int64_t)K * K; i += kThreads) T[i] = E[i];
+    __syncthreads();
+    jacobi_eigh(T, VE, K, sm);
+    double lmax = 0.0;
+    for (int i = 0; i < K; ++i) lmax = fmax(lmax, T[(int64_t)i * K + i].x);
+    const double ltol = lmax * (sizeof(TB) == 16 ? 1e-13 : 1e-7);
+    int r = 0;
+    int* keep = (int*)(dyn_smem + 32768);
+    if (threadIdx.x == 0)
+        for (int i = 0; i < K; ++i)
+            if (T[(int64_t)i * K + i].x > ltol && lmax > 0.0) keep[r++] = i;
+    if (threadIdx.x == 0) sm.flag = r;
+    __syncthreads();
+    r = sm.flag;
+    __syncthreads();
+    if (r == 0) return;
+    for (int64_t idx = threadIdx.x; idx < (int64_t)K * r; idx += kThreads) {
+        const int i = (int)(idx / r), j = (int)(idx % r);
+        const int kj = keep[j];
+        P1[idx] = cscale(VE[(int64_t)i * K + kj], 1.0 / sqrt(T[(int64_t)kj * K + kj].x));
+    }
+    __syncthreads();
+    // T = F^dag E C E F  (r x r):  WT = E F (K x r), VE = C WT, T = WT^dag VE
+    small_gemm(WT, E, P1, K, K, r, false);
+    small_gemm(VE, Cm, WT, K, K, r, false);
+    small_gemm(T, WT, VE, r, K, r, true);
+    jacobi_eigh(T, Cm, r, sm);                 // eigenvectors of T in Cm (r x r)
+    // accept eigenvalues >= thr, largest first
+    int* order = keep + 256;
+    if (threadIdx.x == 0) {
+        int cnt = 0;
+        for (int i = 0; i < r; ++i) order[cnt++] = i;
+        for (int i = 0; i < cnt; ++i)
+            for (int j = i + 1; j < cnt; ++j)
+                if (T[(int64_t)order[j] * r + order[j]].x > T[(int64_t)order[i] * r + order[i]].x) {
+                    const int tmp = order[i]; order[i] = order[j]; order[j] = tmp;
+                }
+        int p = 0;
+        while (p < cnt && p < cap && T[(int64_t)order[p] * r + order[p]].x >= thr) ++p;
+        sm.flag = p;
+    }
+    __syncthreads();
+    const int p = sm.flag;
+    __syncthreads();
+    if (p == 0) return;
+    // coefficients g_i = F w_i (K x p) in E, then u_i = X' g_i (NJ x p, FP64) in the output
+    for (int64_t idx = threadIdx.x; idx < (int64_t)K * p; idx += kThreads) {
+        const int i = (int)(idx / p), j = (int)(idx % p);
+        double2 acc = make_double2(0.0, 0.0);
+        for (int l = 0; l < r; ++l) acc = cadd(acc, cmul(P1[(int64_t)i * r + l], Cm[(int64_t)l * r + order[j]]));
+        E[idx] = acc;
+    }
+    __syncthreads();
+    double* hdr = in.spawn_out;
+    double2* U = (double2*)(hdr + 4 + TTN_SPAWN_MAX_NEW);
+    for (int64_t idx = threadIdx.x; idx < (int64_t)NJ * p; idx += kThreads) {
+        const int J = (int)(idx % NJ), j = (int)(idx / NJ);
+        double2 acc = make_double2(0.0, 0.0);
+        for (int a = 0; a < A; ++a)
+            for (int n = 0; n < chi; ++n)
+                acc = cadd(acc, cmul(cd(X[a * smax + (int64_t)J * chi + n]), E[(int64_t)(a * chi + n) * p + j]));
+        U[idx] = acc;
+    }
+    __syncthreads();
+    // two Gram-Schmidt passes in FP64 against the existing functions and the earlier new ones
+    const TS* Ac = (const TS*)op.c;
+    for (int j = 0; j < p; ++j) {
+        double2* u = U + (int64_t)j * NJ;
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int n = 0; n < chi + j; ++n) {
+                double2 part = make_double2(0.0, 0.0);
+                for (int J = threadIdx.x; J < NJ; J += kThreads) {
+                    const double2 b = n < chi ? cd(Ac[(int64_t)J * chi + n]) : U[(int64_t)(n - chi) * NJ + J];
+                    part = cadd(part, cconjmul(b, u[J]));
+                }
+                const double2 h = block_sum(part, sm);
+                for (int J = threadIdx.x; J < NJ; J += kThreads) {
+                    const double2 b = n < chi ? cd(Ac[(int64_t)J * chi + n]) : U[(int64_t)(n - chi) * NJ + J];
+                    u[J] = csub(u[J], cmul(h, b));
+                }
+                __syncthreads();
+            }
+        }
+        double2 part = make_double2(0.0, 0.0);
+        for (int J = threadIdx.x; J < NJ; J += kThreads) part.x += cabs2(u[J]);
+        const double nrm = sqrt(block_sum(part, sm).x);
+        for (int J = threadIdx.x; J < NJ; J += kThreads) u[J] = cscale(u[J], 1.0 / nrm);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        hdr[0] = op.node; hdr[1] = op.child; hdr[2] = p; hdr[3] = NJ;
+        for (int j = 0; j < p; ++j) hdr[4 + j] = sqrt(fmax(0.0, T[(int64_t)order[j] * r + order[j]].x));
+        __threadfence();
+        atomicExch(in.status, TTN_STATUS_SPAWN_HIT);
+    }
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // interpreter: TS = node tensor / bond type, TB = bulk type
 // ---------------------------------------------------------------------------
@@ -901,6 +1272,9 @@ __device__ void run_op(const TtnOp& op, const TtnInstance& in, double dt, Smem& 
         __syncthreads();
         break;
     }
+    case TTN_OP_SPAWN:
+        spawn_op<TS, TB>(op, in, sm, V, in.smax, t1, t2, Wc, Qc);
+        break;
     case TTN_OP_STEP_END:
         if (threadIdx.x == 0) {
             const int s = *in.steps_done;

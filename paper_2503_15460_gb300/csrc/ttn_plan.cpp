@@ -643,13 +643,14 @@ struct Builder {
 
     // cached per-node / per-bond operator entry ranges
     std::vector<std::vector<std::pair<int, int>>> heff_combo, bond_combo;
-    std::vector<std::pair<int, int>> heff_rng, bond_rng, up_rng;
+    std::vector<std::pair<int, int>> heff_rng, bond_rng, up_rng, bond_raw_rng;
     std::vector<std::vector<std::pair<int, int>>> down_rng;
 
     void prepare_entries() {
         int n = t.n;
         heff_combo.assign(n, {}); bond_combo.assign(n, {});
         heff_rng.assign(n, {0, 0}); bond_rng.assign(n, {0, 0}); up_rng.assign(n, {0, 0});
+        bond_raw_rng.assign(n, {0, 0});
         down_rng.assign(n, {});
         std::vector<std::vector<Proto>> heff(n), bond(n);
         for (int z = 0; z < n; ++z) {
@@ -667,6 +668,7 @@ struct Builder {
                 auto bs = combine(bond[z], {t.bond[z], t.bond[z]}, br);
                 for (auto& rd : br) bond_combo[z].push_back(push_entries(rd));
                 bond_rng[z] = push_entries(bs);
+                bond_raw_rng[z] = push_entries(bond[z]);
                 up_rng[z] = push_entries(up_entries[z]);
             }
         }
@@ -763,6 +765,45 @@ struct Builder {
             emit_qr_up(pr, c);
             emit_env_up(pr, c);
             emit_absorb_parent(pr, z, k);
+        }
+    }
+
+    // Subspace-expansion pass (paper Sec. II.D): the sweep order of S with
+    // the centre moved by QR but no time evolution; the SPAWN op of a bond
+    // stops the program when it accepts new functions.
+    void emit_spawn_visit(Program& pr, int z) {
+        for (size_t k = 0; k < t.ch[z].size(); ++k) {
+            int c = t.ch[z][k];
+            OpSpec s = tensor_op(TTN_OP_SPAWN, z, (int)k);
+            s.op.c = nullptr;
+            s.b_off = p.tensor_off[c];          // child tensor (linked as op.b, copied to op.c)
+            s.op.Dc = (int)t.dims[c].size();
+            for (int j = 0; j < s.op.Dc; ++j) s.op.dimsc[j] = t.dims[c][j];
+            s.op.e0 = up_rng[c].first; s.op.ne = up_rng[c].second;
+            s.op.e1 = down_rng[z][k].first; s.op.ne1 = down_rng[z][k].second;
+            s.op.e2 = bond_raw_rng[c].first; s.op.ne2 = bond_raw_rng[c].second;
+            s.op.node = z; s.op.child = c;
+            s.out_off = p.spawn_out_off;
+            pr.ops.push_back(s);
+            emit_qr_down(pr, z, (int)k);
+            emit_absorb_child(pr, c);
+            emit_env_down(pr, z, (int)k);
+            emit_spawn_visit(pr, c);
+            emit_qr_up(pr, c);
+            emit_env_up(pr, c);
+            emit_absorb_parent(pr, z, (int)k);
+        }
+    }
+    void make_to_root() {
+        p.to_root_prog.assign(t.n, {});
+        for (int z = 1; z < t.n; ++z) {
+            Program& pr = p.to_root_prog[z];
+            for (int u = z; u > 0; u = t.parent[u]) {
+                int par = t.parent[u];
+                int k = (int)(std::find(t.ch[par].begin(), t.ch[par].end(), u) - t.ch[par].begin());
+                emit_qr_up(pr, u);
+                emit_absorb_parent(pr, par, k);
+            }
         }
     }
 
@@ -899,6 +940,13 @@ std::string make_plan(const Tree& t, const Hamiltonian* h, int precision, Plan& 
     p.flops_off = off; off += 64;
     p.cycles_off = off; off += 32 * 8;
     p.scal_off = off; off = align_up(off + 16 * 16, 256);
+    {
+        int64_t maxNJ = 1;
+        for (int c = 1; c < t.n; ++c) maxNJ = std::max<int64_t>(maxNJ, t.size[c] / t.bond[c]);
+        p.spawn_out_off = off;
+        p.spawn_out_bytes = align_up(8 * (4 + TTN_SPAWN_MAX_NEW) + 16 * maxNJ * TTN_SPAWN_MAX_NEW, 256);
+        off += p.spawn_out_bytes;
+    }
     p.max_stamps = 4096;
     p.stamps_off = off; off = align_up(off + 8 * (int64_t)p.max_stamps, 256);
     p.total_bytes = off;
@@ -912,6 +960,20 @@ std::string make_plan(const Tree& t, const Hamiltonian* h, int precision, Plan& 
             if (z > 0) b.emit_env_up(p.init_prog, z);
         b.emit_S(p.step_prog, 0);
         b.emit_Sstar(p.step_prog, 0);
+        b.emit_spawn_visit(p.spawn_prog, 0);
+        b.make_to_root();
+        // spawn workspace: K = (distinct up channels of a bond's terms) x bond dimension
+        int kmax = 0;
+        for (int c = 1; c < t.n; ++c) {
+            std::set<int> ids;
+            auto rg = b.bond_raw_rng[c];
+            for (int i = 0; i < rg.second; ++i)
+                if (p.entries[rg.first + i].slot[0] >= 0) ids.insert(p.entries[rg.first + i].slot[0]);
+            kmax = std::max(kmax, (int)ids.size() * t.bond[c]);
+        }
+        p.spawn_kmax = std::min(kmax, 256);
+        p.spawn_ws_off = p.total_bytes;
+        p.total_bytes = align_up(p.total_bytes + 16 * (p.smax + 6 * (int64_t)p.spawn_kmax * p.spawn_kmax), 256);
         OpSpec s;
         std::memset(&s.op, 0, sizeof(TtnOp));
         s.op.type = TTN_OP_STEP_END;

@@ -77,6 +77,12 @@ struct Plan {
 
     Program init_prog;               // environment build after a state / Hamiltonian change
     Program step_prog;               // one time step
+    Program spawn_prog;              // subspace-expansion pass (stops at the first bond that grows)
+    std::vector<Program> to_root_prog;   // per node: move the orthogonality centre from it to the root
+    int64_t spawn_out_off = 0;       // bytes: spawn result area
+    int64_t spawn_out_bytes = 0;
+    int64_t spawn_ws_off = 0;        // bytes: FP64 spawn workspace (a tensor + 6 K x K matrices)
+    int spawn_kmax = 0;
     // observables
     Program norm_energy_prog;        // out scalars 0: <A,A>, 1: <A,HA>
     std::vector<Program> rdm_prog;   // per leaf: gram walk + reduced density (slot rdm_slot[leaf])

@@ -31,8 +31,14 @@ enum TtnOpType : int {
     TTN_OP_DOT = 8,          // out scalar <- <a, H a> (ne > 0) or <a, a> (ne == 0)
     TTN_OP_TRACE = 9,        // out scalar <- sum_ab slot0[a,b] * slot1[b,a]   (k = dim)
     TTN_OP_CONTRACT_VEC = 10,// a' <- contraction of tensor a with matrices on modes (vacuum projection)
-    TTN_OP_STEP_END = 11     // end of one time step (timestamp, step counter)
+    TTN_OP_STEP_END = 11,    // end of one time step (timestamp, step counter)
+    TTN_OP_SPAWN = 12        // subspace expansion test of the bond to child k (centre at a)
 };
+
+// Status word value left by a SPAWN op that accepted new single-particle
+// functions: the program stops so that the host can grow the bond.
+#define TTN_STATUS_SPAWN_HIT 100
+#define TTN_SPAWN_MAX_NEW 16
 
 struct TtnEntry {
     double wr, wi;          // complex weight
@@ -58,6 +64,15 @@ struct TtnOp {
     void* a;                // main operand
     void* b;                // bond buffer / second operand / output tensor
     double* out;            // DOT / TRACE: complex scalar output (2 doubles)
+    // SPAWN: the child tensor, its index dimensions (children / physical, then
+    // the bond), and the entry ranges of the child's up channels (e0/ne), of
+    // the down channels of the bond built at this node (e1/ne1) and of the
+    // ungrouped bond terms (e2/ne2: slot[0] up channel, slot[1] down channel)
+    void* c;
+    int Dc;
+    int dimsc[TTN_MAXD];
+    int e1, ne1, e2, ne2;
+    int node, child;
 };
 
 struct TtnInstance {
@@ -76,5 +91,11 @@ struct TtnInstance {
     double ktol;
     double qtol;            // QR rank threshold relative to ||M||_F
     int kmax;
-    int pad;
+    int chi_max;            // SPAWN: bond-dimension cap
+    double spawn_eps;       // SPAWN: accept dt * sigma >= spawn_eps
+    double spawn_dt;
+    double* spawn_out;      // SPAWN result: [node, child, p, NJ, sigma_1..p] then p vectors of NJ complex128
+    void* spawn_ws;         // SPAWN FP64 workspace: one tensor copy + 6 dense K x K matrices
+    int spawn_kmax;         // largest K the workspace holds
+    int pad2;
 };

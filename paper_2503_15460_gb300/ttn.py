@@ -291,10 +291,21 @@ class Context:
     def vacuum_projection(self, keep_leaf):
         return ttn_vacuum_projection(self.h, keep_leaf, int(self.tree.phys_dim[keep_leaf]))
 
+    def bond_dims(self):
+        return ttn_bond_dims(self.h, self.tree.n)
+
+    def mode_dims(self, z, bond=None):
+        """Index dimensions of node z with the context's current bond dimensions."""
+        bond = self.bond_dims() if bond is None else bond
+        t = self.tree
+        first = [int(t.phys_dim[z])] if t.phys_dim[z] > 0 else [int(bond[c]) for c in t.children(z)]
+        return first + [int(bond[z]) if z > 0 else 1]
+
     def get_state(self):
-        sizes = [int(np.prod(self.tree.mode_dims(z))) for z in range(self.tree.n)]
-        flat = ttn_get_state(self.h, sizes)
-        return [f.reshape(self.tree.mode_dims(z)) for z, f in enumerate(flat)]
+        bond = self.bond_dims()
+        dims = [self.mode_dims(z, bond) for z in range(self.tree.n)]
+        flat = ttn_get_state(self.h, [int(np.prod(d)) for d in dims])
+        return [f.reshape(d) for f, d in zip(flat, dims)]
 
     def close(self):
         if self.h:
