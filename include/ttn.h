@@ -107,6 +107,32 @@ typedef struct {
 ttn_status ttn_create(int n_nodes, const int* parent, const int* phys_dim,
                       const int* bond_dim, int precision, ttn_ctx** out);
 
+/* Same as ttn_create, but the context holds no device memory yet: its
+ * tensors, Hamiltonian and plan stay on the host until ttn_materialize (or
+ * the first call that needs the device, which materialises it).  Device
+ * memory of such a context comes from the stream-ordered allocator
+ * (cudaMallocAsync on the context's stream).  This is how requests wait in
+ * a ttn_server queue without holding device memory. */
+ttn_status ttn_create_host(int n_nodes, const int* parent, const int* phys_dim,
+                           const int* bond_dim, int precision, ttn_ctx** out);
+
+/* Make the context resident: allocate its arenas (ttn_footprint bytes),
+ * upload operators and tensors, and build the environments.  No-op when it
+ * is resident.  TTN_E_OOM leaves it on the host, unchanged. */
+ttn_status ttn_materialize(ttn_ctx* ctx);
+
+/* Copy the tensors and the step counters to the host and release the
+ * context's device memory; device time stamps and cycle counters are
+ * dropped.  Any later call that needs the device materialises it again
+ * (ttn_get_state, ttn_bond_dims and ttn_step_stats do not). */
+ttn_status ttn_evict(ttn_ctx* ctx);
+
+/* Device bytes the context holds when resident (its state arena: tensors,
+ * bond buffer, Krylov workspace, counters; and its operator arena: SOP
+ * matrices, environments, term tables, op lists), from its plan; valid
+ * whether or not it is resident.  Admission by a ttn_server uses it. */
+ttn_status ttn_footprint(const ttn_ctx* ctx, size_t* bytes);
+
 /* Set every node tensor.  tensors holds the tensors back to back, node z at
  * tensors[offsets[z] .. offsets[z+1]) (offsets has n_nodes+1 entries; sizes
  * must match the node shapes).  The caller promises canonical gauge with
@@ -251,6 +277,91 @@ ttn_status ttn_set_stream(ttn_ctx* ctx, void* cuda_stream);
 
 /* Device memory held by the context, in bytes. */
 ttn_status ttn_device_bytes(const ttn_ctx* ctx, size_t* bytes);
+
+/* ---------------------------------------------------------------------
+ * Request server: continuous batching of independent propagations.
+ *
+ * The paper runs one propagation at a time; this is a serving layer over
+ * the same step (Sec. II.C) for many independent requests on one device --
+ * parameter sweeps over couplings, temperatures or bath discretisations.
+ * A request is a context (tree, state, Hamiltonian) and (dt, nsteps).
+ * Submitted requests wait in a FIFO queue holding no device memory (the
+ * context is moved to the host).  ttn_server_pump admits queued requests
+ * while fewer than max_slots are admitted and the sum of their footprints
+ * (ttn_footprint) stays within hbm_budget; an admitted context keeps its
+ * tensors and environments on the device until it finishes.  Each pump
+ * waits for the previous launch, retires finished requests (their device
+ * time stamps are recorded, their tensors copied back to the host context,
+ * their memory returned), admits more, and starts the next launch: one
+ * thread block per admitted context, each running whole steps of its own
+ * dt until its steps are done or the launch's slice of device time is
+ * used up.  Admission of new requests (allocation, upload, environment
+ * build) runs on a second stream while a launch is in flight.  A
+ * context's results do not depend on the other contexts in the launch nor
+ * on how its steps are split over launches: they equal ttn_step's.
+ * The server is driven by one host thread; it is not thread-safe.
+ * --------------------------------------------------------------------- */
+typedef struct ttn_server ttn_server;
+
+typedef struct {
+    size_t hbm_budget;   /* bytes the admitted contexts may hold together;
+                            0 = 90% of the device's free memory at creation */
+    int max_slots;       /* most contexts admitted at once; 0 = 2 per SM    */
+    double slice_ms;     /* device time per launch (at least one step of the
+                            slowest admitted context); 0 = 20 ms           */
+    int use_graph;       /* 1: each launch is the replay of one CUDA graph
+                            (table upload, kernel, result read-back)        */
+} ttn_server_opts;
+
+typedef struct {
+    int64_t submitted, completed, failed, queued, running;
+    int64_t steps;        /* steps run for all requests                     */
+    int64_t launches;
+    int64_t peak_running; /* most contexts admitted at once                 */
+    size_t bytes_in_use, peak_bytes;   /* sums of admitted footprints       */
+    double p50_step_ms, p99_step_ms;   /* per-step latency: interval between
+                            consecutive step completions of one request
+                            (device time stamps), over finished requests    */
+    int64_t n_latencies;
+} ttn_server_stats;
+
+/* Create a server on the current device for contexts of one precision.
+ * opts may be NULL (defaults; use_graph = 1). */
+ttn_status ttn_server_create(int precision, const ttn_server_opts* opts, ttn_server** out);
+
+/* Queue ctx for nsteps steps of dt (opts: Krylov / QR settings; expand
+ * must be 0; NULL = defaults).  The context must have a Hamiltonian and the
+ * server's precision; a resident context is moved to the host first.  The
+ * caller keeps ownership but must not use ctx until its ticket is returned
+ * by ttn_server_poll (afterwards ctx is host-resident and usable; on
+ * failure it is marked failed, see ttn_last_error). */
+ttn_status ttn_server_submit(ttn_server* srv, ttn_ctx* ctx, double dt, int nsteps,
+                             const ttn_step_opts* opts, int64_t* ticket);
+
+/* One scheduling round (see above).  Returns after starting the next launch
+ * (it does not wait for it).  n_running / n_queued may be NULL. */
+ttn_status ttn_server_pump(ttn_server* srv, int* n_running, int* n_queued);
+
+/* Pump until every submitted request has finished. */
+ttn_status ttn_server_drain(ttn_server* srv);
+
+/* Tickets of requests finished since the last poll (up to max), with their
+ * status: TTN_OK, TTN_E_OOM (footprint larger than the budget), or the
+ * device status that stopped it. */
+ttn_status ttn_server_poll(ttn_server* srv, int max, int64_t* tickets, ttn_status* status, int* n);
+
+/* Counters and per-step latency percentiles of the server. */
+ttn_status ttn_server_get_stats(ttn_server* srv, ttn_server_stats* out);
+
+/* Every recorded per-step latency (ms), in recording order (up to max). */
+ttn_status ttn_server_latencies(ttn_server* srv, double* out_ms, int64_t max, int64_t* n);
+
+/* Message for the server's most recent failure. */
+const char* ttn_server_last_error(const ttn_server* srv);
+
+/* Wait for the launch in flight, move admitted contexts back to the host
+ * (unfinished) and release the server.  NULL is ignored. */
+void ttn_server_destroy(ttn_server* srv);
 
 /* Message for the most recent failure of a call on ctx (or of ttn_create
  * when ctx is NULL).  Valid until the next call on the same context. */

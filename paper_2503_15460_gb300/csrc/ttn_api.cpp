@@ -9,52 +9,17 @@
 #include <vector>
 
 #include "../../include/ttn.h"
+#include "ttn_ctx.hpp"
 #include "ttn_launch.h"
 #include "ttn_plan.hpp"
 
 using ttn::cplx;
 
+using ttn::DevProgram;
+
 namespace {
 
 thread_local std::string g_create_error;
-
-struct DevProgram {
-    TtnOp* d_ops = nullptr;
-    int n_ops = 0;
-};
-
-}  // namespace
-
-struct ttn_ctx {
-    int precision = 0;
-    ttn::Tree tree;
-    ttn::Hamiltonian ham;
-    bool has_h = false;
-    ttn::Plan plan;
-    cudaStream_t stream = nullptr;
-    int device = 0;
-    std::string err;
-    bool failed = false;
-
-    char* d_state = nullptr;       // tensors, bond, workspace, status, scalars, stamps
-    size_t state_bytes = 0;
-    char* d_ops = nullptr;         // slot storage, slot table, entries, op lists, instances
-    size_t ops_bytes = 0;
-    TtnSlot* d_slots = nullptr;
-    TtnEntry* d_entries = nullptr;
-    DevProgram init_p, step_p, ne_p, spawn_p;
-    std::vector<DevProgram> rdm_p, vac_p, to_root_p;
-    TtnInstance* d_inst = nullptr; // staging for single-instance launches
-    TtnInstance* d_batch = nullptr;
-    int batch_cap = 0;
-    double ktol = 0.0;
-    double qtol = 0.0;
-    int kmax = TTN_KMAX;
-    int64_t steps_total = 0;
-    int64_t spawned = 0;            // single-particle functions added by expansion
-};
-
-namespace {
 
 ttn_status fail(ttn_ctx* c, ttn_status s, const std::string& msg) {
     if (c) {
@@ -94,7 +59,9 @@ void from_bulk(const char* src, size_t n, size_t esz, cplx* dst) {
     for (size_t i = 0; i < n; ++i) dst[i] = cplx(f[2 * i], f[2 * i + 1]);
 }
 
-TtnInstance make_instance(ttn_ctx* c, const DevProgram& p) {
+}  // namespace
+
+TtnInstance ttn::make_instance(ttn_ctx* c, const DevProgram& p) {
     TtnInstance in{};
     in.ops = p.d_ops;
     in.n_ops = p.n_ops;
@@ -115,6 +82,54 @@ TtnInstance make_instance(ttn_ctx* c, const DevProgram& p) {
     in.spawn_ws = c->d_state + c->plan.spawn_ws_off;
     in.spawn_kmax = c->plan.spawn_kmax;
     return in;
+}
+
+ttn_status ttn::ctx_fail(ttn_ctx* c, ttn_status s, const std::string& msg) { return fail(c, s, msg); }
+
+namespace {
+
+using ttn::make_instance;
+
+cudaError_t dev_alloc(ttn_ctx* c, char** p, size_t n) {
+    return c->pooled ? cudaMallocAsync((void**)p, n, c->stream) : cudaMalloc((void**)p, n);
+}
+
+void dev_free(ttn_ctx* c, char* p) {
+    if (!p) return;
+    if (c->pooled) cudaFreeAsync(p, c->stream);
+    else cudaFree(p);
+}
+
+// Allocation failure: TTN_E_OOM, context left as it was; other errors fail it.
+ttn_status alloc_fail(ttn_ctx* c, cudaError_t e, const char* what) {
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(c, TTN_E_OOM, std::string(what) + ": out of device memory");
+    }
+    return cuda_fail(c, e, what);
+}
+
+// Layout of the operator arena: slot storage, slot table, entries, ops, instance.
+struct OpsLayout {
+    size_t slot_bytes, off_table, off_entries, off_ops, off_inst, total;
+};
+
+OpsLayout ops_layout(const ttn::Plan& P) {
+    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+    OpsLayout L{};
+    for (auto& s : P.slots) L.slot_bytes = std::max(L.slot_bytes, (size_t)s.off + (size_t)s.rows * s.cols * P.esz);
+    L.slot_bytes = al(L.slot_bytes);
+    size_t n_ops_total = P.init_prog.ops.size() + P.step_prog.ops.size() + P.norm_energy_prog.ops.size() +
+                         P.spawn_prog.ops.size();
+    for (auto& p : P.rdm_prog) n_ops_total += p.ops.size();
+    for (auto& p : P.vac_prog) n_ops_total += p.ops.size();
+    for (auto& p : P.to_root_prog) n_ops_total += p.ops.size();
+    L.off_table = L.slot_bytes;
+    L.off_entries = al(L.off_table + P.slots.size() * sizeof(TtnSlot));
+    L.off_ops = al(L.off_entries + std::max<size_t>(1, P.entries.size()) * sizeof(TtnEntry));
+    L.off_inst = al(L.off_ops + std::max<size_t>(1, n_ops_total) * sizeof(TtnOp));
+    L.total = al(L.off_inst + sizeof(TtnInstance));
+    return L;
 }
 
 ttn_status check_status(ttn_ctx* c) {
@@ -148,7 +163,7 @@ ttn_status check_status_spawn(ttn_ctx* c, bool* hit) {
 }
 
 void free_ops(ttn_ctx* c) {
-    if (c->d_ops) cudaFree(c->d_ops);
+    dev_free(c, c->d_ops);
     c->d_ops = nullptr;
     c->ops_bytes = 0;
     c->d_slots = nullptr;
@@ -161,23 +176,14 @@ void free_ops(ttn_ctx* c) {
 // Allocate and fill the operator arena for the current plan.
 ttn_status upload_ops(ttn_ctx* c) {
     ttn::Plan& P = c->plan;
-    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
-    size_t slot_bytes = 0;
-    for (auto& s : P.slots) slot_bytes = std::max(slot_bytes, (size_t)s.off + (size_t)s.rows * s.cols * P.esz);
-    slot_bytes = al(slot_bytes);
-    std::vector<const ttn::Program*> progs{&P.init_prog, &P.step_prog, &P.norm_energy_prog, &P.spawn_prog};
-    for (auto& p : P.rdm_prog) progs.push_back(&p);
-    for (auto& p : P.vac_prog) progs.push_back(&p);
-    for (auto& p : P.to_root_prog) progs.push_back(&p);
-    size_t n_ops_total = 0;
-    for (auto* p : progs) n_ops_total += p->ops.size();
-    size_t off_table = slot_bytes;
-    size_t off_entries = al(off_table + P.slots.size() * sizeof(TtnSlot));
-    size_t off_ops = al(off_entries + std::max<size_t>(1, P.entries.size()) * sizeof(TtnEntry));
-    size_t off_inst = al(off_ops + std::max<size_t>(1, n_ops_total) * sizeof(TtnOp));
-    size_t total = al(off_inst + sizeof(TtnInstance));
+    const OpsLayout L = ops_layout(P);
+    const size_t off_table = L.off_table, off_entries = L.off_entries, off_ops = L.off_ops, off_inst = L.off_inst;
+    const size_t total = L.total;
     free_ops(c);
-    CK(cudaMalloc(&c->d_ops, total), "cudaMalloc (operators)");
+    char* arena = nullptr;
+    cudaError_t ae = dev_alloc(c, &arena, total);
+    if (ae != cudaSuccess) return alloc_fail(c, ae, "device allocation (operators)");
+    c->d_ops = arena;
     c->ops_bytes = total;
     std::vector<char> host(total, 0);
     // constant slots
@@ -229,6 +235,19 @@ ttn_status upload_ops(ttn_ctx* c) {
 
 ttn_status upload_state(ttn_ctx* c, const std::vector<std::vector<cplx>>& A);
 
+// Node tensors of a resident context, copied to the host.
+ttn_status download_state(ttn_ctx* c, std::vector<std::vector<cplx>>& A) {
+    std::vector<char> raw(c->plan.bond_off);
+    CK(cudaMemcpyAsync(raw.data(), c->d_state, raw.size(), cudaMemcpyDeviceToHost, c->stream), "state copy");
+    CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+    A.assign(c->tree.n, {});
+    for (int u = 0; u < c->tree.n; ++u) {
+        const cplx* src = (const cplx*)(raw.data() + c->plan.tensor_off[u]);
+        A[u].assign(src, src + c->tree.size[u]);
+    }
+    return TTN_OK;
+}
+
 // Grow the bond of `child` by the p functions in U (NJ x p, column j of the
 // new block = U[j*NJ ..]): append them to the child's tensor, zero-pad the
 // parent's index, and rebuild plan, arenas, centre position and
@@ -238,14 +257,9 @@ ttn_status grow_bond(ttn_ctx* c, int child, int p, const std::vector<cplx>& U) {
     ttn::Tree& t = c->tree;
     const int z = t.parent[child];
     const int k = (int)(std::find(t.ch[z].begin(), t.ch[z].end(), child) - t.ch[z].begin());
-    std::vector<char> raw(c->plan.bond_off);
-    CK(cudaMemcpyAsync(raw.data(), c->d_state, raw.size(), cudaMemcpyDeviceToHost, c->stream), "state copy");
-    CK(cudaStreamSynchronize(c->stream), "stream synchronize");
-    std::vector<std::vector<cplx>> A(t.n);
-    for (int u = 0; u < t.n; ++u) {
-        const cplx* src = (const cplx*)(raw.data() + c->plan.tensor_off[u]);
-        A[u].assign(src, src + t.size[u]);
-    }
+    std::vector<std::vector<cplx>> A;
+    ttn_status ds = download_state(c, A);
+    if (ds) return ds;
     const int chi = t.bond[child];
     const int64_t NJ = t.size[child] / chi;
     // child: [NJ x chi] -> [NJ x (chi + p)]
@@ -274,8 +288,9 @@ ttn_status grow_bond(ttn_ctx* c, int child, int p, const std::vector<cplx>& U) {
     msg = ttn::make_plan(nt, &c->ham, c->precision, P);
     if (!msg.empty()) return fail(c, TTN_E_STATE, msg);
     char* fresh = nullptr;
-    CK(cudaMalloc(&fresh, P.total_bytes), "cudaMalloc (state)");
-    cudaFree(c->d_state);
+    cudaError_t ae = dev_alloc(c, &fresh, P.total_bytes);
+    if (ae != cudaSuccess) { c->failed = true; return alloc_fail(c, ae, "device allocation (state)"); }
+    dev_free(c, c->d_state);
     c->d_state = fresh;
     c->state_bytes = P.total_bytes;
     CK(cudaMemsetAsync(c->d_state, 0, c->state_bytes, c->stream), "memset");
@@ -333,17 +348,37 @@ ttn_status upload_state(ttn_ctx* c, const std::vector<std::vector<cplx>>& A) {
 ttn_status usable(ttn_ctx* c) {
     if (!c) return TTN_E_INVALID;
     if (c->failed) return fail(c, TTN_E_STATE, "context is in a failed state: " + c->err);
+    if (!c->resident) return TTN_OK;      // host-resident: no device work until materialised
     cudaError_t e = cudaSetDevice(c->device);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
     return TTN_OK;
 }
 
-}  // namespace
+// usable() and resident on the device.
+ttn_status ready(ttn_ctx* c) {
+    ttn_status u = usable(c);
+    if (u) return u;
+    if (!c->resident) {
+        cudaError_t e = cudaSetDevice(c->device);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    }
+    return ttn::ctx_materialize(c);
+}
 
-extern "C" {
+// Tensors given by the caller: to the device (resident) or kept on the host.
+ttn_status take_state(ttn_ctx* c, std::vector<std::vector<cplx>>& A) {
+    if (!c->resident) {
+        c->host_A.swap(A);
+        return TTN_OK;
+    }
+    ttn_status s = upload_state(c, A);
+    if (s) return s;
+    if (c->has_h) return run_program(c, c->init_p, 0.0, 1);
+    return TTN_OK;
+}
 
-ttn_status ttn_create(int n_nodes, const int* parent, const int* phys_dim, const int* bond_dim, int precision,
-                      ttn_ctx** out) {
+ttn_status create_ctx(int n_nodes, const int* parent, const int* phys_dim, const int* bond_dim, int precision,
+                      bool on_host, ttn_ctx** out) {
     if (!out) return fail(nullptr, TTN_E_INVALID, "out is NULL");
     *out = nullptr;
     if (precision != TTN_FP64 && precision != TTN_MIXED) return fail(nullptr, TTN_E_INVALID, "precision must be TTN_FP64 or TTN_MIXED");
@@ -356,6 +391,17 @@ ttn_status ttn_create(int n_nodes, const int* parent, const int* phys_dim, const
     c->tree = t;
     cudaGetDevice(&c->device);
     ttn::make_plan(c->tree, nullptr, precision, c->plan);
+    std::vector<std::vector<cplx>> vecs(t.n), A;
+    for (int z = 0; z < t.n; ++z)
+        if (t.leaf(z)) { vecs[z].assign(t.phys[z], 0.0); vecs[z][0] = 1.0; }
+    ttn::product_state(t, vecs, A);
+    if (on_host) {
+        c->resident = false;
+        c->pooled = true;
+        c->host_A.swap(A);
+        *out = c;
+        return TTN_OK;
+    }
     cudaError_t e = cudaMalloc(&c->d_state, c->plan.total_bytes);
     if (e != cudaSuccess) {
         g_create_error = std::string("cudaMalloc (state): ") + cudaGetErrorString(e);
@@ -366,13 +412,92 @@ ttn_status ttn_create(int n_nodes, const int* parent, const int* phys_dim, const
     cudaMemset(c->d_state, 0, c->state_bytes);
     ttn_status s = upload_ops(c);
     if (s != TTN_OK) { g_create_error = c->err; ttn_destroy(c); return s; }
-    std::vector<std::vector<cplx>> vecs(t.n), A;
-    for (int z = 0; z < t.n; ++z)
-        if (t.leaf(z)) { vecs[z].assign(t.phys[z], 0.0); vecs[z][0] = 1.0; }
-    ttn::product_state(t, vecs, A);
     s = upload_state(c, A);
     if (s != TTN_OK) { g_create_error = c->err; ttn_destroy(c); return s; }
     *out = c;
+    return TTN_OK;
+}
+
+}  // namespace
+
+size_t ttn::ctx_footprint(const ttn_ctx* c) { return (size_t)c->plan.total_bytes + ops_layout(c->plan).total; }
+
+ttn_status ttn::ctx_materialize(ttn_ctx* c) {
+    if (c->resident) return TTN_OK;
+    char* st = nullptr;
+    cudaError_t ae = dev_alloc(c, &st, c->plan.total_bytes);
+    if (ae != cudaSuccess) return alloc_fail(c, ae, "device allocation (state)");
+    c->d_state = st;
+    c->state_bytes = c->plan.total_bytes;
+    c->resident = true;
+    CK(cudaMemsetAsync(c->d_state, 0, c->state_bytes, c->stream), "memset");
+    ttn_status s = upload_ops(c);
+    if (s) {
+        // give the memory back and stay on the host
+        free_ops(c);
+        dev_free(c, c->d_state);
+        c->d_state = nullptr; c->state_bytes = 0; c->resident = false;
+        return s;
+    }
+    const int steps = (int)c->saved_steps;
+    const double flops = c->saved_flops;
+    CK(cudaMemcpyAsync(c->d_state + c->plan.steps_off, &steps, sizeof(int), cudaMemcpyHostToDevice, c->stream), "counter upload");
+    CK(cudaMemcpyAsync(c->d_state + c->plan.flops_off, &flops, sizeof(double), cudaMemcpyHostToDevice, c->stream), "counter upload");
+    s = upload_state(c, c->host_A);     // synchronises the stream
+    if (s) return s;
+    c->host_A.clear();
+    c->host_A.shrink_to_fit();
+    if (c->has_h) return run_program(c, c->init_p, 0.0, 1);
+    return TTN_OK;
+}
+
+ttn_status ttn::ctx_evict(ttn_ctx* c) {
+    if (!c->resident) return TTN_OK;
+    std::vector<std::vector<cplx>> A;
+    ttn_status s = download_state(c, A);
+    if (s) return s;
+    int steps = 0;
+    double flops = 0.0;
+    CK(cudaMemcpyAsync(&steps, c->d_state + c->plan.steps_off, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "counter copy");
+    CK(cudaMemcpyAsync(&flops, c->d_state + c->plan.flops_off, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "counter copy");
+    CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+    free_ops(c);
+    dev_free(c, c->d_state);
+    c->d_state = nullptr;
+    c->state_bytes = 0;
+    if (c->d_batch) cudaFree(c->d_batch);
+    c->d_batch = nullptr;
+    c->batch_cap = 0;
+    c->host_A.swap(A);
+    c->saved_steps = steps;
+    c->saved_flops = flops;
+    c->resident = false;
+    CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+    return TTN_OK;
+}
+
+extern "C" {
+
+ttn_status ttn_create(int n_nodes, const int* parent, const int* phys_dim, const int* bond_dim, int precision,
+                      ttn_ctx** out) {
+    return create_ctx(n_nodes, parent, phys_dim, bond_dim, precision, false, out);
+}
+
+ttn_status ttn_create_host(int n_nodes, const int* parent, const int* phys_dim, const int* bond_dim, int precision,
+                           ttn_ctx** out) {
+    return create_ctx(n_nodes, parent, phys_dim, bond_dim, precision, true, out);
+}
+
+ttn_status ttn_materialize(ttn_ctx* c) { return ready(c); }
+
+ttn_status ttn_evict(ttn_ctx* c) {
+    ttn_status u = usable(c); if (u) return u;
+    return ttn::ctx_evict(c);
+}
+
+ttn_status ttn_footprint(const ttn_ctx* c, size_t* bytes) {
+    if (!c || !bytes) return TTN_E_INVALID;
+    *bytes = ttn::ctx_footprint(c);
     return TTN_OK;
 }
 
@@ -388,10 +513,7 @@ ttn_status ttn_set_state(ttn_ctx* c, const ttn_c128* tensors, const int64_t* off
         for (auto& v : A[z])
             if (!std::isfinite(v.real()) || !std::isfinite(v.imag())) return fail(c, TTN_E_INVALID, "non-finite tensor entry");
     }
-    ttn_status s = upload_state(c, A);
-    if (s) return s;
-    if (c->has_h) return run_program(c, c->init_p, 0.0, 1);
-    return TTN_OK;
+    return take_state(c, A);
 }
 
 ttn_status ttn_set_product_state(ttn_ctx* c, const ttn_c128* leaf_vecs, const int64_t* leaf_offsets) {
@@ -407,10 +529,7 @@ ttn_status ttn_set_product_state(ttn_ctx* c, const ttn_c128* leaf_vecs, const in
         if (!(nrm > 0) || !std::isfinite(nrm)) return fail(c, TTN_E_INVALID, "leaf vector " + std::to_string(z) + " is zero or not finite");
     }
     ttn::product_state(c->tree, vecs, A);
-    ttn_status s = upload_state(c, A);
-    if (s) return s;
-    if (c->has_h) return run_program(c, c->init_p, 0.0, 1);
-    return TTN_OK;
+    return take_state(c, A);
 }
 
 ttn_status ttn_set_sop_hamiltonian(ttn_ctx* c, int n_terms, const ttn_c128* coeff, const int* term_ptr,
@@ -426,19 +545,26 @@ ttn_status ttn_set_sop_hamiltonian(ttn_ctx* c, int n_terms, const ttn_c128* coef
     ttn::Plan P;
     msg = ttn::make_plan(c->tree, &h, c->precision, P);
     if (!msg.empty()) return fail(c, TTN_E_INVALID, msg);
-    c->ham = h;
-    c->has_h = true;
-    c->plan = P;
+    if (!c->resident) {
+        c->ham = h;
+        c->has_h = true;
+        c->plan = P;
+        return TTN_OK;
+    }
     if ((size_t)P.total_bytes > c->state_bytes) {
         char* fresh = nullptr;
-        CK(cudaMalloc(&fresh, P.total_bytes), "cudaMalloc (state)");
+        cudaError_t ae = dev_alloc(c, &fresh, P.total_bytes);
+        if (ae != cudaSuccess) return alloc_fail(c, ae, "device allocation (state)");
         CK(cudaMemsetAsync(fresh, 0, P.total_bytes, c->stream), "memset");
         CK(cudaMemcpyAsync(fresh, c->d_state, P.bond_off, cudaMemcpyDeviceToDevice, c->stream), "state copy");
         CK(cudaStreamSynchronize(c->stream), "stream synchronize");
-        cudaFree(c->d_state);
+        dev_free(c, c->d_state);
         c->d_state = fresh;
         c->state_bytes = P.total_bytes;
     }
+    c->ham = h;
+    c->has_h = true;
+    c->plan = P;
     ttn_status s = upload_ops(c);
     if (s) { c->failed = true; return s; }
     return run_program(c, c->init_p, 0.0, 1);
@@ -447,6 +573,7 @@ ttn_status ttn_set_sop_hamiltonian(ttn_ctx* c, int n_terms, const ttn_c128* coef
 ttn_status ttn_step(ttn_ctx* c, double dt, int nsteps, const ttn_step_opts* opts) {
     ttn_status u = usable(c); if (u) return u;
     if (!c->has_h) return fail(c, TTN_E_STATE, "no Hamiltonian set");
+    u = ready(c); if (u) return u;
     if (nsteps < 0 || !std::isfinite(dt)) return fail(c, TTN_E_INVALID, "bad dt / nsteps");
     if (opts) {
         if (opts->krylov_maxdim > TTN_KMAX) return fail(c, TTN_E_INVALID, "krylov_maxdim must be <= 32");
@@ -472,6 +599,7 @@ ttn_status ttn_step_batch(ttn_ctx* const* ctxs, int n, double dt, int nsteps, co
     for (int i = 0; i < n; ++i) {
         ttn_status u = usable(ctxs[i]); if (u) return u;
         if (!ctxs[i]->has_h) return fail(ctxs[i], TTN_E_STATE, "no Hamiltonian set");
+        u = ready(ctxs[i]); if (u) return u;
         if (ctxs[i]->precision != c->precision) return fail(c, TTN_E_INVALID, "mixed precisions in one batch");
         if (opts) {
             if (opts->expand) return fail(c, TTN_E_INVALID, "subspace expansion is run per context: use ttn_step");
@@ -501,7 +629,7 @@ ttn_status ttn_step_batch(ttn_ctx* const* ctxs, int n, double dt, int nsteps, co
 }
 
 ttn_status ttn_norm_energy(ttn_ctx* c, double* norm2, ttn_c128* energy) {
-    ttn_status u = usable(c); if (u) return u;
+    ttn_status u = ready(c); if (u) return u;
     ttn_status s = run_program(c, c->ne_p, 0.0, 1);
     if (s) return s;
     double sc[4] = {0, 0, 0, 0};
@@ -517,7 +645,7 @@ ttn_status ttn_norm_energy(ttn_ctx* c, double* norm2, ttn_c128* energy) {
 }
 
 ttn_status ttn_reduced_density(ttn_ctx* c, int leaf, ttn_c128* out) {
-    ttn_status u = usable(c); if (u) return u;
+    ttn_status u = ready(c); if (u) return u;
     if (leaf < 0 || leaf >= c->tree.n || !c->tree.leaf(leaf) || !out) return fail(c, TTN_E_INVALID, "leaf must be a leaf node");
     ttn_status s = run_program(c, c->rdm_p[leaf], 0.0, 1);
     if (s) return s;
@@ -561,7 +689,7 @@ ttn_status ttn_expect(ttn_ctx* c, int n_obs, const int* leaf, const ttn_c128* op
 }
 
 ttn_status ttn_vacuum_projection(ttn_ctx* c, int keep_leaf, ttn_c128* out) {
-    ttn_status u = usable(c); if (u) return u;
+    ttn_status u = ready(c); if (u) return u;
     if (keep_leaf < 0 || keep_leaf >= c->tree.n || !c->tree.leaf(keep_leaf) || !out) return fail(c, TTN_E_INVALID, "keep_leaf must be a leaf");
     ttn_status s = run_program(c, c->vac_p[keep_leaf], 0.0, 1);
     if (s) return s;
@@ -576,14 +704,17 @@ ttn_status ttn_vacuum_projection(ttn_ctx* c, int keep_leaf, ttn_c128* out) {
 
 ttn_status ttn_get_state(ttn_ctx* c, ttn_c128* tensors, int64_t* offsets) {
     if (!c || !tensors || !offsets) return TTN_E_INVALID;
-    cudaSetDevice(c->device);
-    std::vector<char> raw(c->plan.bond_off);
-    CK(cudaMemcpyAsync(raw.data(), c->d_state, raw.size(), cudaMemcpyDeviceToHost, c->stream), "state copy");
-    CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+    std::vector<std::vector<cplx>> A;
+    if (c->resident) {
+        cudaSetDevice(c->device);
+        ttn_status s = download_state(c, A);
+        if (s) return s;
+    }
+    const auto& src = c->resident ? A : c->host_A;
     int64_t o = 0;
     for (int z = 0; z < c->tree.n; ++z) {
         offsets[z] = o;
-        std::memcpy(tensors + o, raw.data() + c->plan.tensor_off[z], c->tree.size[z] * 16);
+        std::memcpy(tensors + o, src[z].data(), c->tree.size[z] * 16);
         o += c->tree.size[z];
     }
     offsets[c->tree.n] = o;
@@ -704,6 +835,12 @@ ttn_status ttn_set_device(int device) {
 ttn_status ttn_step_stats(ttn_ctx* c, int64_t* steps_done, double* flops, uint64_t* stamps, int max_stamps,
                           int* n_stamps) {
     if (!c) return TTN_E_INVALID;
+    if (!c->resident) {
+        if (steps_done) *steps_done = c->saved_steps;
+        if (flops) *flops = c->saved_flops;
+        if (n_stamps) *n_stamps = 0;
+        return TTN_OK;
+    }
     cudaSetDevice(c->device);
     int steps = 0;
     double fl = 0.0;
@@ -727,6 +864,7 @@ ttn_status ttn_step_stats(ttn_ctx* c, int64_t* steps_done, double* flops, uint64
 
 ttn_status ttn_op_cycles(ttn_ctx* c, uint64_t* cycles) {
     if (!c || !cycles) return TTN_E_INVALID;
+    if (!c->resident) { std::memset(cycles, 0, 32 * 8); return TTN_OK; }
     cudaSetDevice(c->device);
     CK(cudaMemcpyAsync(cycles, c->d_state + c->plan.cycles_off, 32 * 8, cudaMemcpyDeviceToHost, c->stream), "cycles copy");
     CK(cudaStreamSynchronize(c->stream), "stream synchronize");
@@ -752,11 +890,13 @@ const char* ttn_last_error(const ttn_ctx* c) {
 
 void ttn_destroy(ttn_ctx* c) {
     if (!c) return;
+    if (!c->resident && !c->d_batch) { delete c; return; }
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     free_ops(c);
-    if (c->d_state) cudaFree(c->d_state);
+    dev_free(c, c->d_state);
     if (c->d_batch) cudaFree(c->d_batch);
+    if (c->pooled && c->stream) cudaStreamSynchronize(c->stream);
     delete c;
 }
 

@@ -1,0 +1,73 @@
+// Internal view of a context, shared by the C ABI (ttn_api.cpp) and the
+// request server (ttn_server.cpp).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ttn.h"
+#include "ttn_plan.hpp"
+
+namespace ttn {
+
+struct DevProgram {
+    TtnOp* d_ops = nullptr;
+    int n_ops = 0;
+};
+
+}  // namespace ttn
+
+struct ttn_ctx {
+    int precision = 0;
+    ttn::Tree tree;
+    ttn::Hamiltonian ham;
+    bool has_h = false;
+    ttn::Plan plan;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    std::string err;
+    bool failed = false;
+
+    // Residency.  A resident context holds its arenas and tensors on the
+    // device; a host-resident one keeps the tensors in host_A and holds no
+    // device memory.  Pooled contexts take their arenas from the
+    // stream-ordered allocator (cudaMallocAsync on `stream`).
+    bool resident = true;
+    bool pooled = false;
+    std::vector<std::vector<ttn::cplx>> host_A;
+    int64_t saved_steps = 0;
+    double saved_flops = 0.0;
+
+    char* d_state = nullptr;       // tensors, bond, workspace, status, scalars, stamps
+    size_t state_bytes = 0;
+    char* d_ops = nullptr;         // slot storage, slot table, entries, op lists, instances
+    size_t ops_bytes = 0;
+    TtnSlot* d_slots = nullptr;
+    TtnEntry* d_entries = nullptr;
+    ttn::DevProgram init_p, step_p, ne_p, spawn_p;
+    std::vector<ttn::DevProgram> rdm_p, vac_p, to_root_p;
+    TtnInstance* d_inst = nullptr; // staging for single-instance launches
+    TtnInstance* d_batch = nullptr;
+    int batch_cap = 0;
+    double ktol = 0.0;
+    double qtol = 0.0;
+    int kmax = TTN_KMAX;
+    int64_t steps_total = 0;
+    int64_t spawned = 0;            // single-particle functions added by expansion
+};
+
+namespace ttn {
+
+// Device descriptor of one of the context's programs (resident contexts).
+TtnInstance make_instance(ttn_ctx* c, const DevProgram& p);
+// Record a failure on c (or, for c == NULL, for ttn_last_error(NULL)).
+ttn_status ctx_fail(ttn_ctx* c, ttn_status s, const std::string& msg);
+// Bytes ctx_materialize allocates for the current plan.
+size_t ctx_footprint(const ttn_ctx* c);
+// Allocate the arenas, upload operators and tensors, build environments.
+ttn_status ctx_materialize(ttn_ctx* c);
+// Copy the tensors and counters to the host and release the arenas.
+ttn_status ctx_evict(ttn_ctx* c);
+
+}  // namespace ttn

@@ -1294,29 +1294,67 @@ __device__ void run_op(const TtnOp& op, const TtnInstance& in, double dt, Smem& 
     }
 }
 
+__device__ __forceinline__ long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return (long long)t;
+}
+
+// One thread block per instance runs its op list nrep times (nrep < 0: the
+// instance's own count and time step).  With a slice of device time > 0 a
+// block stops after the step that ends its slice; rep_out (optional)
+// receives, per block, the steps run, the status word and the elapsed time.
+// hdr (optional, device memory) supplies the instance count and the slice.
 template <class TS, class TB>
-__global__ void __launch_bounds__(kThreads, 2) program_kernel(const TtnInstance* insts, int n_inst, double dt, int nrep) {
+__global__ void __launch_bounds__(kThreads, 2) program_kernel(const TtnInstance* insts, const TtnLaunchHdr* hdr,
+                                                              int n_inst, double dt, int nrep, long long slice_arg,
+                                                              TtnRepOut* rep_out) {
     __shared__ Smem sm;
+    __shared__ int s_stop;
+    __shared__ long long s_t0;
     const int b = blockIdx.x;
-    if (b >= n_inst) return;
+    const int n = hdr ? hdr->n : n_inst;
+    const long long slice_ns = hdr ? hdr->slice_ns : slice_arg;
+    if (b >= n) return;
     const TtnInstance in = insts[b];
-    if (threadIdx.x == 0) { s_flops = 0.0; for (int i = 0; i < 8; ++i) s_sub[i] = 0; }
+    const double dtb = nrep < 0 ? in.dt : dt;
+    const int nr = nrep < 0 ? in.nrep : nrep;
+    if (threadIdx.x == 0) {
+        s_flops = 0.0;
+        for (int i = 0; i < 8; ++i) s_sub[i] = 0;
+        s_t0 = global_ns();
+        s_stop = 0;
+    }
     __syncthreads();
-    for (int rep = 0; rep < nrep; ++rep) {
+    int rep = 0;
+    while (rep < nr) {
         for (int o = 0; o < in.n_ops; ++o) {
             if (threadIdx.x == 0) sm.flag = *((volatile int*)in.status);
             __syncthreads();
             if (sm.flag != 0) break;
             const TtnOp op = in.ops[o];
             const long long c0 = clock64();
-            run_op<TS, TB>(op, in, dt, sm);
+            run_op<TS, TB>(op, in, dtb, sm);
             if (threadIdx.x == 0 && in.op_cycles) atomicAdd(&in.op_cycles[op.type & 15], (unsigned long long)(clock64() - c0));
         }
         if (sm.flag != 0) break;
+        ++rep;
+        if (slice_ns > 0) {
+            if (threadIdx.x == 0) s_stop = global_ns() - s_t0 >= slice_ns;
+            __syncthreads();
+            if (s_stop) break;
+        }
     }
     if (threadIdx.x == 0 && in.flops) atomicAdd(in.flops, s_flops);
     if (threadIdx.x == 0 && in.op_cycles)
         for (int i = 0; i < 8; ++i) atomicAdd(&in.op_cycles[16 + i], s_sub[i]);
+    if (threadIdx.x == 0 && rep_out) {
+        TtnRepOut r;
+        r.reps = rep;
+        r.status = *((volatile int*)in.status);
+        r.elapsed_ns = global_ns() - s_t0;
+        rep_out[b] = r;
+    }
 }
 
 // One thread block applies a sum-of-products operator to one tensor (the
@@ -1347,16 +1385,30 @@ int ttn_launch_heff(const TtnEntry* d_entries, int ne, const TtnSlot* d_slots, i
     return (int)cudaGetLastError();
 }
 
+int ttn_program_init() {
+    static std::once_flag once;
+    static cudaError_t err = cudaSuccess;
+    std::call_once(once, [] {
+        err = cudaFuncSetAttribute(program_kernel<double2, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStageBytes);
+        if (err == cudaSuccess)
+            err = cudaFuncSetAttribute(program_kernel<double2, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStageBytes);
+    });
+    return (int)err;
+}
+
 int ttn_launch_program(int precision, const TtnInstance* d_insts, int n_inst, double dt, int nrep, cudaStream_t s) {
-    if (n_inst <= 0) return 0;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(program_kernel<double2, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStageBytes);
-        cudaFuncSetAttribute(program_kernel<double2, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStageBytes);
-        attr_set = true;
-    }
-    if (precision == 0) program_kernel<double2, double2><<<n_inst, kThreads, kStageBytes, s>>>(d_insts, n_inst, dt, nrep);
-    else program_kernel<double2, float2><<<n_inst, kThreads, kStageBytes, s>>>(d_insts, n_inst, dt, nrep);
+    return ttn_launch_program_ex(precision, d_insts, nullptr, n_inst, dt, nrep, 0, nullptr, s);
+}
+
+int ttn_launch_program_ex(int precision, const TtnInstance* d_insts, const TtnLaunchHdr* d_hdr, int grid, double dt,
+                          int nrep, long long slice_ns, TtnRepOut* d_rep_out, cudaStream_t s) {
+    if (grid <= 0) return 0;
+    int e = ttn_program_init();
+    if (e) return e;
+    if (precision == 0)
+        program_kernel<double2, double2><<<grid, kThreads, kStageBytes, s>>>(d_insts, d_hdr, grid, dt, nrep, slice_ns, d_rep_out);
+    else
+        program_kernel<double2, float2><<<grid, kThreads, kStageBytes, s>>>(d_insts, d_hdr, grid, dt, nrep, slice_ns, d_rep_out);
     return (int)cudaGetLastError();
 }
 

@@ -9,6 +9,19 @@
 int ttn_launch_program(int precision, const TtnInstance* d_insts, int n_inst, double dt, int nrep,
                        cudaStream_t stream);
 
+// General form: `grid` blocks.  With d_hdr (device memory) the first
+// d_hdr->n blocks run and d_hdr->slice_ns replaces slice_ns; without it all
+// `grid` blocks run.  nrep < 0 takes each instance's own step count and
+// time step (TtnInstance::nrep, ::dt).  slice_ns > 0 ends a block after the
+// step that uses up its slice of device time.  d_rep_out (optional, `grid`
+// entries) receives what each block did.
+int ttn_launch_program_ex(int precision, const TtnInstance* d_insts, const TtnLaunchHdr* d_hdr, int grid, double dt,
+                          int nrep, long long slice_ns, TtnRepOut* d_rep_out, cudaStream_t stream);
+
+// Set the kernel attributes once per process (call before capturing a
+// launch into a CUDA graph).  Returns a cudaError_t code.
+int ttn_program_init();
+
 // Apply a sum-of-products operator (entries, factor slots) to the complex128
 // tensor x (dims[0..D-1]) into y with one thread block; t1..t3 are scratch
 // tensors of prod(dims) complex128 elements each.  Returns a cudaError_t code.

@@ -97,5 +97,22 @@ struct TtnInstance {
     double* spawn_out;      // SPAWN result: [node, child, p, NJ, sigma_1..p] then p vectors of NJ complex128
     void* spawn_ws;         // SPAWN FP64 workspace: one tensor copy + 6 dense K x K matrices
     int spawn_kmax;         // largest K the workspace holds
-    int pad2;
+    int nrep;               // steps this launch when the launch asks for per-instance counts
+    double dt;              // time step for the same case
+};
+
+// Launch parameters read from device memory (so one captured launch can be
+// replayed with a different instance count and time slice).
+struct TtnLaunchHdr {
+    int n;                  // instances in the table
+    int pad;
+    long long slice_ns;     // device time per block, 0 = unlimited
+};
+
+// What one block reports after a launch that asked for it: whole steps run,
+// the instance's status word, and the block's device time (globaltimer ns).
+struct TtnRepOut {
+    int reps;
+    int status;
+    long long elapsed_ns;
 };

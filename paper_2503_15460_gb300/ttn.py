@@ -31,6 +31,19 @@ class ttn_step_opts(C.Structure):
                 ("qr_rank_tol", C.c_double)]
 
 
+class ttn_server_opts(C.Structure):
+    _fields_ = [("hbm_budget", C.c_size_t), ("max_slots", C.c_int), ("slice_ms", C.c_double),
+                ("use_graph", C.c_int)]
+
+
+class ttn_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
+                ("queued", C.c_int64), ("running", C.c_int64), ("steps", C.c_int64),
+                ("launches", C.c_int64), ("peak_running", C.c_int64), ("bytes_in_use", C.c_size_t),
+                ("peak_bytes", C.c_size_t), ("p50_step_ms", C.c_double), ("p99_step_ms", C.c_double),
+                ("n_latencies", C.c_int64)]
+
+
 _P = C.c_void_p
 _I32 = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 _I64 = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
@@ -39,6 +52,10 @@ _F64 = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
 
 _sig = {
     "ttn_create": ([C.c_int, _I32, _I32, _I32, C.c_int, C.POINTER(_P)], C.c_int),
+    "ttn_create_host": ([C.c_int, _I32, _I32, _I32, C.c_int, C.POINTER(_P)], C.c_int),
+    "ttn_materialize": ([_P], C.c_int),
+    "ttn_evict": ([_P], C.c_int),
+    "ttn_footprint": ([_P, C.POINTER(C.c_size_t)], C.c_int),
     "ttn_set_state": ([_P, _C128, _I64], C.c_int),
     "ttn_set_product_state": ([_P, _C128, _I64], C.c_int),
     "ttn_set_sop_hamiltonian": ([_P, C.c_int, _C128, _I32, _I32, _C128, _I64, C.c_int], C.c_int),
@@ -61,6 +78,15 @@ _sig = {
     "ttn_device_bytes": ([_P, C.POINTER(C.c_size_t)], C.c_int),
     "ttn_last_error": ([_P], C.c_char_p),
     "ttn_destroy": ([_P], None),
+    "ttn_server_create": ([C.c_int, C.POINTER(ttn_server_opts), C.POINTER(_P)], C.c_int),
+    "ttn_server_submit": ([_P, _P, C.c_double, C.c_int, C.POINTER(ttn_step_opts), C.POINTER(C.c_int64)], C.c_int),
+    "ttn_server_pump": ([_P, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
+    "ttn_server_drain": ([_P], C.c_int),
+    "ttn_server_poll": ([_P, C.c_int, _I64, _I32, C.POINTER(C.c_int)], C.c_int),
+    "ttn_server_get_stats": ([_P, C.POINTER(ttn_server_stats)], C.c_int),
+    "ttn_server_latencies": ([_P, _F64, C.c_int64, C.POINTER(C.c_int64)], C.c_int),
+    "ttn_server_last_error": ([_P], C.c_char_p),
+    "ttn_server_destroy": ([_P], None),
 }
 for _name, (_args, _res) in _sig.items():
     _f = getattr(_lib, _name)
@@ -94,6 +120,30 @@ def ttn_create(parent, phys_dim, bond_dim, precision=TTN_FP64):
     st = _lib.ttn_create(len(parent), parent, phys, bond, int(precision), C.byref(h))
     _check(st, None)
     return h
+
+
+def ttn_create_host(parent, phys_dim, bond_dim, precision=TTN_FP64):
+    parent = np.ascontiguousarray(parent, dtype=np.int32)
+    phys = np.ascontiguousarray(phys_dim, dtype=np.int32)
+    bond = np.ascontiguousarray(bond_dim, dtype=np.int32)
+    h = _P()
+    st = _lib.ttn_create_host(len(parent), parent, phys, bond, int(precision), C.byref(h))
+    _check(st, None)
+    return h
+
+
+def ttn_materialize(ctx):
+    _check(_lib.ttn_materialize(ctx), ctx)
+
+
+def ttn_evict(ctx):
+    _check(_lib.ttn_evict(ctx), ctx)
+
+
+def ttn_footprint(ctx):
+    n = C.c_size_t(0)
+    _check(_lib.ttn_footprint(ctx, C.byref(n)), ctx)
+    return n.value
 
 
 def _flatten(tensors):
@@ -258,16 +308,126 @@ def ttn_destroy(ctx):
     _lib.ttn_destroy(ctx)
 
 
+def _server_check(st, srv):
+    if st != TTN_OK:
+        m = _lib.ttn_server_last_error(srv)
+        raise TTNError(st, m.decode() if m else "")
+
+
+def ttn_server_create(precision=TTN_MIXED, hbm_budget=0, max_slots=0, slice_ms=0.0, use_graph=1):
+    o = ttn_server_opts(int(hbm_budget), int(max_slots), float(slice_ms), int(use_graph))
+    h = _P()
+    st = _lib.ttn_server_create(int(precision), C.byref(o), C.byref(h))
+    if st != TTN_OK:
+        raise TTNError(st, "ttn_server_create failed")
+    return h
+
+
+def ttn_server_submit(srv, ctx, dt, nsteps, opts=None):
+    t = C.c_int64(0)
+    _server_check(_lib.ttn_server_submit(srv, ctx, float(dt), int(nsteps), _opts(opts), C.byref(t)), srv)
+    return t.value
+
+
+def ttn_server_pump(srv):
+    r, q = C.c_int(0), C.c_int(0)
+    _server_check(_lib.ttn_server_pump(srv, C.byref(r), C.byref(q)), srv)
+    return r.value, q.value
+
+
+def ttn_server_drain(srv):
+    _server_check(_lib.ttn_server_drain(srv), srv)
+
+
+def ttn_server_poll(srv, max_n=4096):
+    t = np.zeros(max(1, max_n), dtype=np.int64)
+    s = np.zeros(max(1, max_n), dtype=np.int32)
+    n = C.c_int(0)
+    _server_check(_lib.ttn_server_poll(srv, int(max_n), t, s, C.byref(n)), srv)
+    return list(zip(t[:n.value].tolist(), s[:n.value].tolist()))
+
+
+def ttn_server_get_stats(srv):
+    st = ttn_server_stats()
+    _server_check(_lib.ttn_server_get_stats(srv, C.byref(st)), srv)
+    return {k: getattr(st, k) for k, _ in ttn_server_stats._fields_}
+
+
+def ttn_server_latencies(srv, max_n=1 << 22):
+    out = np.zeros(max(1, max_n), dtype=np.float64)
+    n = C.c_int64(0)
+    _server_check(_lib.ttn_server_latencies(srv, out, int(max_n), C.byref(n)), srv)
+    return out[:n.value].copy()
+
+
+def ttn_server_last_error(srv) -> str:
+    m = _lib.ttn_server_last_error(srv)
+    return m.decode() if m else ""
+
+
+def ttn_server_destroy(srv):
+    _lib.ttn_server_destroy(srv)
+
+
+class Server:
+    """Owns one ttn_server (continuous batching of contexts; include/ttn.h)."""
+
+    def __init__(self, precision=TTN_MIXED, hbm_budget=0, max_slots=0, slice_ms=0.0, use_graph=True):
+        self.h = ttn_server_create(precision, hbm_budget, max_slots, slice_ms, int(bool(use_graph)))
+
+    def submit(self, ctx, dt, nsteps, opts=None):
+        return ttn_server_submit(self.h, ctx.h, dt, nsteps, opts)
+
+    def pump(self):
+        return ttn_server_pump(self.h)
+
+    def drain(self):
+        ttn_server_drain(self.h)
+
+    def poll(self):
+        return ttn_server_poll(self.h)
+
+    def stats(self):
+        return ttn_server_get_stats(self.h)
+
+    def latencies(self):
+        return ttn_server_latencies(self.h)
+
+    def close(self):
+        if self.h:
+            ttn_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # ---------------------------------------------------------------------------
 # convenience wrapper around a context handle
 # ---------------------------------------------------------------------------
 class Context:
     """Owns one ttn_ctx.  ``tree`` is a workloads.Tree (parent/phys_dim/bond_dim)."""
 
-    def __init__(self, tree, precision=TTN_FP64):
+    def __init__(self, tree, precision=TTN_FP64, on_host=False):
         self.tree = tree
         self.precision = precision
-        self.h = ttn_create(tree.parent, tree.phys_dim, tree.bond_dim, precision)
+        make = ttn_create_host if on_host else ttn_create
+        self.h = make(tree.parent, tree.phys_dim, tree.bond_dim, precision)
+
+    def footprint(self):
+        return ttn_footprint(self.h)
+
+    def device_bytes(self):
+        return ttn_device_bytes(self.h)
+
+    def evict(self):
+        ttn_evict(self.h)
+
+    def materialize(self):
+        ttn_materialize(self.h)
 
     def set_state(self, tensors):
         ttn_set_state(self.h, tensors)

@@ -1,0 +1,78 @@
+"""Host-resident contexts (ttn_create_host): the host logic behind admission
+by device-memory footprint, exercised without a GPU."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2503_15460_gb300 import ttn
+    return ttn
+
+
+def host_ctx(lib, p, precision=None):
+    c = lib.Context(p.tree, lib.TTN_MIXED if precision is None else precision, on_host=True)
+    c.set_state(p.tensors)
+    c.set_hamiltonian(p.H)
+    return c
+
+
+def test_host_context_holds_no_device_memory(lib):
+    p = W.config_c1()
+    c = host_ctx(lib, p)
+    assert c.device_bytes() == 0
+    assert c.footprint() > 0
+    for a, b in zip(c.get_state(), p.tensors):
+        assert np.array_equal(a, b)
+    assert np.array_equal(c.bond_dims()[1:], p.tree.bond_dim[1:])
+    steps, flops, stamps = lib.ttn_step_stats(c.h)
+    assert steps == 0 and flops == 0.0 and stamps.size == 0
+    c.evict()                       # already on the host: no-op
+    c.close()
+
+
+def test_footprint_grows_with_bond_dimension(lib):
+    small = host_ctx(lib, W.config_c2(bonds=(6, 4, 3, 2), d_range=(4, 6)))
+    large = host_ctx(lib, W.config_c2(bonds=(12, 8, 6, 4), d_range=(4, 6)))
+    assert large.footprint() > small.footprint()
+    # complex128 bulk storage needs more than the mixed form of the same problem
+    p = W.config_c2(bonds=(6, 4, 3, 2), d_range=(4, 6))
+    assert host_ctx(lib, p, lib.TTN_FP64).footprint() > host_ctx(lib, p, lib.TTN_MIXED).footprint()
+
+
+def test_footprint_covers_krylov_workspace(lib):
+    """The state arena holds (Krylov dimension + 4) workspace vectors of the
+    largest node tensor, so the footprint is at least that."""
+    p = W.config_c2(bonds=(6, 4, 3, 2), d_range=(4, 6))
+    smax = max(int(np.prod(a.shape)) for a in p.tensors)
+    c = host_ctx(lib, p, lib.TTN_FP64)
+    assert c.footprint() >= (32 + 4) * smax * 16
+
+
+def test_host_context_validates_hamiltonian(lib):
+    p = W.config_c1()
+    c = lib.Context(p.tree, lib.TTN_MIXED, on_host=True)
+    H = W.SOP()
+    H.add(1.0, (0, np.eye(2)))      # node 0 is not a leaf
+    with pytest.raises(lib.TTNError) as e:
+        c.set_hamiltonian(H)
+    assert e.value.status == lib.TTN_E_INVALID
+    c.close()
+
+
+def test_request_generator_shapes():
+    """Serving requests: the stated ranges and both model families."""
+    rs = W.config_c5_requests(64, seed=5)
+    assert {r["kind"] for r in rs} == {"sb", "vib"}
+    for r in rs:
+        assert 8 <= r["n_modes"] <= 128 and 8 <= r["d"] <= 20 and 8 <= r["chi"] <= 48
+        assert 100 <= r["steps"] <= 400
+    small = W.config_c5_requests(6, seed=5, n_modes_range=(3, 6), d_range=(4, 6), chi_range=(2, 4),
+                                 steps_range=(4, 8))
+    for r in small:
+        p = W.c5_problem(r)
+        assert p.nsteps == r["steps"]
+        assert p.dt == (0.05 if r["kind"] == "sb" else 0.1)
+        assert len(p.obs_leaves) == r["n_modes"] + 1

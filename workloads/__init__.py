@@ -562,6 +562,43 @@ def config_c4(K_matsubara: int = 15, depth: int = 10, chi: int = 24, lam: float 
                    {"sys": sysl, "a": a_l, "b": b_l, "alpha": al, "nu": nu, "Hs": Hs})
 
 
+def vibronic_balanced_problem(n_modes: int, d: int, chi: int, seed: int, dt: float = 0.1,
+                              delta: float = 0.1, nsteps: int = 100) -> Problem:
+    """Two-state vibronic model with the parameter recipe of config_c2
+    (seeded) on root(el, balanced binary tree over n_modes leaves of local
+    dimension d), interior bonds chi.  Initial |1> x vacuum."""
+    rng = np.random.default_rng(seed)
+    omega = rng.uniform(0.05, 0.5, n_modes)
+    kappa = rng.normal(0.0, 0.05, (n_modes, 2))
+    n_quad = int(round(0.2 * n_modes))
+    quad = np.sort(rng.choice(n_modes, n_quad, replace=False))
+    gq = rng.normal(0.0, 0.01, (n_quad, 2))
+    n_lam = min(3, n_modes)
+    lam_modes = np.sort(rng.choice(n_modes, n_lam, replace=False))
+    lam = rng.normal(0.0, 0.05, n_lam)
+    d_modes = np.full(n_modes, d)
+    bath = [("leaf", d, min(chi, d), f"m{k}") for k in range(n_modes)]
+    t = build_tree(("node", 1, [("leaf", 2, 2, "el"), balanced_spec(bath, chi)]))
+    el = t.leaf_of_label("el")
+    modes = [t.leaf_of_label(f"m{i}") for i in range(n_modes)]
+    H = vibronic_sop(el, modes, d_modes, omega, kappa, gq, quad, lam, lam_modes, delta)
+    v = np.zeros(2, dtype=np.complex128); v[1] = 1.0
+    A = product_state(t, {el: v})
+    return Problem(f"vibronic_2x{n_modes}_d{d}_chi{chi}_seed{seed}", t, H, A, dt, nsteps, [el] + modes,
+                   {"el": el, "modes": modes, "d_modes": d_modes})
+
+
+def c5_problem(req: dict) -> Problem:
+    """The propagation one serving request asks for: spin-boson (dt 0.05) or
+    two-state vibronic (dt 0.1) on a balanced binary tree, with the request's
+    modes, local and bond dimensions and step count."""
+    if req["kind"] == "sb":
+        return spin_boson_star_problem(req["n_modes"], req["d"], req["chi"], req["alpha"], beta=req["beta"],
+                                       dt=0.05, nsteps=req["steps"], name=f"req{req['id']}_spin_boson")
+    return vibronic_balanced_problem(req["n_modes"], req["d"], req["chi"], req["seed"], dt=0.1,
+                                     nsteps=req["steps"])
+
+
 def config_c5_requests(n_requests: int = 512, seed: int = 5, n_modes_range=(8, 128),
                        d_range=(8, 20), chi_range=(8, 48), steps_range=(100, 400)):
     """Seeded request parameters for the serving stream: half spin-boson
