@@ -15,6 +15,7 @@ instance) are reported beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B]
     python bench.py --impl reference ...     # the CPU oracle on the same workload
+    python bench.py --serve                  # serving stream through ttn_server (own JSON line)
 """
 from __future__ import annotations
 
@@ -37,8 +38,11 @@ METRIC = "TTN-TDVP steps/s: batched mixed-precision vs FP64 at <=1e-6 pop. error
 UNIT = "steps/s"
 DT = 0.1
 FP32_LANES_PER_SM = 128
+FP64_LANES_PER_SM = 2          # 1/64 of the FP32 rate on GB300
 N_SM = 152
 SM_MAX_MHZ = 2070.0
+PEAK_FP32 = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12   # TFLOP/s
+PEAK_FP64 = N_SM * FP64_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
 
 def measured_traffic(batch):
@@ -150,7 +154,7 @@ def run_ours(args, rank, world, local_rank):
     handles = [c.h for c in ctxs]
     for _ in range(args.warmup):
         ttn.ttn_step_batch(handles, DT, 1)
-    fl0 = sum(ttn.ttn_step_stats(h, 1)[1] for h in handles)
+    fl0 = np.sum([ttn.ttn_flop_counts(h) for h in handles], axis=0)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     torch.cuda.synchronize()
@@ -170,8 +174,8 @@ def run_ours(args, rank, world, local_rank):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     clocks = clk.summary()
-    fl1 = sum(ttn.ttn_step_stats(h, 1)[1] for h in handles)
-    flops_per_step = (fl1 - fl0) / args.steps
+    fl1 = np.sum([ttn.ttn_flop_counts(h) for h in handles], axis=0)
+    flops_per_step, flops64_per_step = (fl1 - fl0) / args.steps
     lat = []
     for h in handles:
         _, _, st = ttn.ttn_step_stats(h, args.steps + 1)
@@ -249,7 +253,25 @@ def run_ours(args, rank, world, local_rank):
 
     for c in ctxs:
         c.close()
-    return dict(ms=ms, value=value, flops_per_step=flops_per_step, lat=lat, clocks=clocks, fp64=fp64, e2e=e2e)
+    return dict(ms=ms, value=value, flops_per_step=float(flops_per_step), flops64_per_step=float(flops64_per_step),
+                lat=lat, clocks=clocks, fp64=fp64, e2e=e2e)
+
+
+def alu_roofline(flops, flops64, seconds, traffic):
+    """Per-pipe utilisation of one step: FP32 work against the FP32 lanes,
+    FP64 work against the FP64 lanes; the pipe with the larger lower bound
+    on time is the one that binds."""
+    f32 = flops - flops64
+    a32, a64 = f32 / seconds / 1e12, flops64 / seconds / 1e12
+    pipes = {"fp32": {"achieved": a32, "peak": PEAK_FP32, "frac": a32 / PEAK_FP32, "flops_per_step": f32},
+             "fp64": {"achieved": a64, "peak": PEAK_FP64, "frac": a64 / PEAK_FP64, "flops_per_step": flops64}}
+    bind = max(pipes, key=lambda k: pipes[k]["frac"])
+    b = pipes[bind]
+    return {"bound": "alu", "pipe": bind, "achieved": b["achieved"], "peak": b["peak"], "unit": "TFLOP/s",
+            "frac": b["frac"], "traffic": traffic,
+            "peak_source": (f"derived: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 / {FP64_LANES_PER_SM} FP64 lanes "
+                            f"x 2 flop x {SM_MAX_MHZ:.0f} MHz (the measured peaks hold no FP32 / FP64 entry)"),
+            "pipes": pipes, "flops_per_step": flops}
 
 
 def cpu_baseline(args):
@@ -304,6 +326,111 @@ def run_reference(args, rank, world):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# serving stream (continuous batching through ttn_server)
+# ---------------------------------------------------------------------------
+SERVE_RANGES = dict(n_modes_range=(8, 128), d_range=(8, 20), chi_range=(4, 16), steps_range=(20, 80))
+
+
+def serve_workload_name(n):
+    r = SERVE_RANGES
+    return (f"{n} seeded requests, half spin-boson (dt 0.05, alpha U[0.05,1], beta in {{inf,5,1}}) and half "
+            f"two-state vibronic (dt 0.1), balanced binary trees, modes {r['n_modes_range']}, local dims "
+            f"{r['d_range']}, bond dims {r['chi_range']}, steps {r['steps_range']}")
+
+
+def run_serving(args):
+    """Serving stream: all requests at t0 (burst), then Poisson arrivals at
+    80 % of the burst's measured capacity; reference: requests one at a time
+    in FP64 on a sample, extrapolated by step count."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2503_15460_gb300 import ttn
+    import workloads as W
+    ttn.ttn_set_device(0)
+    reqs = W.config_c5_requests(args.serve_requests, seed=5, **SERVE_RANGES)
+    probs = [W.c5_problem(r) for r in reqs]
+    total_steps = sum(p.nsteps for p in probs)
+
+    def contexts(precision):
+        cs = []
+        for p in probs:
+            c = ttn.Context(p.tree, precision, on_host=True)
+            c.set_state(p.tensors)
+            c.set_hamiltonian(p.H)
+            cs.append(c)
+        return cs
+
+    def run(arrivals):
+        ctxs = contexts(ttn.TTN_MIXED)
+        srv = ttn.Server(ttn.TTN_MIXED, slice_ms=args.slice_ms)
+        order = np.argsort(arrivals, kind="stable")
+        t_arr, t_done, tick = {}, {}, {}
+        nxt = 0
+        t0 = time.perf_counter()
+        while len(t_done) < len(probs):
+            now = time.perf_counter() - t0
+            while nxt < len(order) and arrivals[order[nxt]] <= now:
+                i = int(order[nxt])
+                tick[srv.submit(ctxs[i], probs[i].dt, probs[i].nsteps)] = i
+                t_arr[i] = now
+                nxt += 1
+            running, queued = srv.pump()
+            if running == 0 and queued == 0 and nxt < len(order):
+                time.sleep(max(0.0, arrivals[order[nxt]] - (time.perf_counter() - t0)))
+            for t, st in srv.poll():
+                if st != ttn.TTN_OK:
+                    raise RuntimeError(f"request {tick[t]} failed with status {st}")
+                t_done[tick[t]] = time.perf_counter() - t0
+        makespan = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        for c in ctxs:
+            c.close()
+        resp = np.array([t_done[i] - t_arr[i] for i in range(len(probs))])
+        return {"steps_per_s": total_steps / makespan, "makespan_s": makespan,
+                "p50_step_ms": st["p50_step_ms"], "p99_step_ms": st["p99_step_ms"],
+                "p50_request_s": float(np.percentile(resp, 50)), "p99_request_s": float(np.percentile(resp, 99)),
+                "launches": st["launches"], "peak_running": st["peak_running"],
+                "peak_bytes": st["peak_bytes"]}
+
+    burst = run(np.zeros(len(probs)))
+    rate = 0.8 * burst["steps_per_s"] / (total_steps / len(probs))        # requests per second
+    rng = np.random.default_rng(55)
+    poisson_arr = np.cumsum(rng.exponential(1.0 / rate, len(probs)))
+    poisson = run(poisson_arr)
+    poisson["arrival_rate_per_s"] = rate
+
+    # reference: one request at a time, complex128, on a sample
+    sample = list(range(min(args.serve_sample, len(probs))))
+    t = 0.0
+    for i in sample:
+        p = probs[i]
+        c = ttn.Context(p.tree, ttn.TTN_FP64)
+        c.set_state(p.tensors)
+        c.set_hamiltonian(p.H)
+        t0 = time.perf_counter()
+        c.step(p.dt, p.nsteps)
+        t += time.perf_counter() - t0
+        c.close()
+    sample_steps = sum(probs[i].nsteps for i in sample)
+    alone_rate = sample_steps / t
+    line = {
+        "metric": "serving: aggregate TTN-TDVP steps/s, continuous batching (mixed) vs one request at a time (FP64)",
+        "value": poisson["steps_per_s"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+        "dtype": "c64 bulk / f64 state", "data": "synthetic",
+        "config": {"workload": serve_workload_name(len(probs)),
+                   "arrivals": "Poisson at 80% of the burst capacity (seed 55)", "slice_ms": args.slice_ms},
+        "poisson": poisson, "burst": burst,
+        "one_at_a_time_fp64": {"value": alone_rate, "unit": UNIT,
+                               "sample": f"first {len(sample)} requests run alone with ttn_step, "
+                                         f"{sample_steps} steps; aggregate rate = steps / time"},
+        "speedup_vs_one_at_a_time_fp64": poisson["steps_per_s"] / alone_rate,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -316,7 +443,13 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=1)
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu", dest="cpu", action="store_false")
+    ap.add_argument("--serve", action="store_true", help="run the serving stream instead (separate JSON line)")
+    ap.add_argument("--serve-requests", type=int, default=512)
+    ap.add_argument("--serve-sample", type=int, default=8)
+    ap.add_argument("--slice-ms", type=float, default=20.0)
     args = ap.parse_args()
+    if args.serve:
+        return run_serving(args)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -330,8 +463,6 @@ def main():
         dist.init_process_group("nccl")
     r = run_ours(args, rank, world, local_rank)
     if rank == 0:
-        peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-        achieved = r["flops_per_step"] / (r["ms"] / args.steps / 1e3) / 1e12
         lat = sorted(r["lat"])
         line = {
             "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -346,10 +477,8 @@ def main():
             "fp64": r["fp64"],
             "speedup_vs_fp64": (r["value"] / r["fp64"]["value"]) if r["fp64"] else None,
             "gpu_launches": args.steps,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": measured_traffic(args.batch),
-                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz (no FP32 entry in the measured peaks)",
-                         "flops_per_step": r["flops_per_step"]},
+            "roofline": alu_roofline(r["flops_per_step"], r["flops64_per_step"], r["ms"] / args.steps / 1e3,
+                                     measured_traffic(args.batch)),
             "clocks": r["clocks"],
             "e2e": r["e2e"],
         }

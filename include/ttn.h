@@ -264,6 +264,14 @@ ttn_status ttn_set_device(int device);
 ttn_status ttn_step_stats(ttn_ctx* ctx, int64_t* steps_done, double* flops, uint64_t* stamps,
                           int max_stamps, int* n_stamps);
 
+/* Algorithmic floating-point operations executed by the context's device
+ * programs since creation (the counter of ttn_step_stats) and the part of
+ * them executed in FP64 arithmetic: QR and bond absorption always, and, in
+ * TTN_FP64 mode, everything.  On GB300 the FP64 pipe runs at 1/64 of the
+ * FP32 rate, so the split tells which pipe bounds a mixed-precision step.
+ * Either pointer may be NULL. */
+ttn_status ttn_flop_counts(ttn_ctx* ctx, double* total, double* fp64);
+
 /* SM clock cycles the context's device programs spent per operation type,
  * cycles[32] (index: 1 QR towards a child, 2 QR towards the parent,
  * 3/4 bond absorption into child/parent, 5 environment builds, 6 operator

@@ -440,9 +440,9 @@ ttn_status ttn::ctx_materialize(ttn_ctx* c) {
         return s;
     }
     const int steps = (int)c->saved_steps;
-    const double flops = c->saved_flops;
+    const double flops[2] = {c->saved_flops, c->saved_flops64};
     CK(cudaMemcpyAsync(c->d_state + c->plan.steps_off, &steps, sizeof(int), cudaMemcpyHostToDevice, c->stream), "counter upload");
-    CK(cudaMemcpyAsync(c->d_state + c->plan.flops_off, &flops, sizeof(double), cudaMemcpyHostToDevice, c->stream), "counter upload");
+    CK(cudaMemcpyAsync(c->d_state + c->plan.flops_off, flops, sizeof(flops), cudaMemcpyHostToDevice, c->stream), "counter upload");
     s = upload_state(c, c->host_A);     // synchronises the stream
     if (s) return s;
     c->host_A.clear();
@@ -457,9 +457,9 @@ ttn_status ttn::ctx_evict(ttn_ctx* c) {
     ttn_status s = download_state(c, A);
     if (s) return s;
     int steps = 0;
-    double flops = 0.0;
+    double flops[2] = {0.0, 0.0};
     CK(cudaMemcpyAsync(&steps, c->d_state + c->plan.steps_off, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "counter copy");
-    CK(cudaMemcpyAsync(&flops, c->d_state + c->plan.flops_off, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "counter copy");
+    CK(cudaMemcpyAsync(flops, c->d_state + c->plan.flops_off, sizeof(flops), cudaMemcpyDeviceToHost, c->stream), "counter copy");
     CK(cudaStreamSynchronize(c->stream), "stream synchronize");
     free_ops(c);
     dev_free(c, c->d_state);
@@ -470,7 +470,8 @@ ttn_status ttn::ctx_evict(ttn_ctx* c) {
     c->batch_cap = 0;
     c->host_A.swap(A);
     c->saved_steps = steps;
-    c->saved_flops = flops;
+    c->saved_flops = flops[0];
+    c->saved_flops64 = flops[1];
     c->resident = false;
     CK(cudaStreamSynchronize(c->stream), "stream synchronize");
     return TTN_OK;
@@ -859,6 +860,19 @@ ttn_status ttn_step_stats(ttn_ctx* c, int64_t* steps_done, double* flops, uint64
             stamps[i] = raw[s % c->plan.max_stamps];
         }
     if (n_stamps) *n_stamps = stamps ? n : 0;
+    return TTN_OK;
+}
+
+ttn_status ttn_flop_counts(ttn_ctx* c, double* total, double* fp64) {
+    if (!c) return TTN_E_INVALID;
+    double f[2] = {c->saved_flops, c->saved_flops64};
+    if (c->resident) {
+        cudaSetDevice(c->device);
+        CK(cudaMemcpyAsync(f, c->d_state + c->plan.flops_off, sizeof(f), cudaMemcpyDeviceToHost, c->stream), "counter copy");
+        CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+    }
+    if (total) *total = f[0];
+    if (fp64) *fp64 = f[1];
     return TTN_OK;
 }
 

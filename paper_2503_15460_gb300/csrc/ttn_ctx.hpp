@@ -38,6 +38,7 @@ struct ttn_ctx {
     std::vector<std::vector<ttn::cplx>> host_A;
     int64_t saved_steps = 0;
     double saved_flops = 0.0;
+    double saved_flops64 = 0.0;
 
     char* d_state = nullptr;       // tensors, bond, workspace, status, scalars, stamps
     size_t state_bytes = 0;

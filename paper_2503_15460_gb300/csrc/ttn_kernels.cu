@@ -29,7 +29,15 @@ constexpr int kWarps = kThreads / 32;
 // Algorithmic floating-point operations of this block (complex multiply-add
 // = 8), accumulated by thread 0 and flushed to the instance counter at exit.
 __shared__ double s_flops;
-__device__ __forceinline__ void count_flops(double f) { if (threadIdx.x == 0) s_flops += f; }
+// The part of them executed in FP64 arithmetic (element type complex128).
+__shared__ double s_flops64;
+template <class T>
+__device__ __forceinline__ void count_flops_t(double f) {
+    if (threadIdx.x == 0) {
+        s_flops += f;
+        if (sizeof(T) == 16) s_flops64 += f;
+    }
+}
 
 // Sub-phase cycle counters (thread 0), flushed with the op counters.
 __shared__ unsigned long long s_sub[8];
@@ -156,7 +164,7 @@ template <class T>
 __device__ double2 block_dot(const T* __restrict__ a, const T* __restrict__ b, int64_t n, Smem& sm) {
     T acc = czero<T>();
     for (int64_t i = threadIdx.x; i < n; i += kThreads) cfmaconj(acc, a[i], b[i]);
-    count_flops(8.0 * n);
+    count_flops_t<T>(8.0 * n);
     return block_sum(cd(acc), sm);
 }
 
@@ -235,7 +243,7 @@ __device__ void mode_prod_tiled(T* __restrict__ out, const T* __restrict__ in, i
 template <class T>
 __device__ void mode_prod(T* __restrict__ out, const T* __restrict__ in, int64_t L, int nin, int nout,
                           int64_t R, const T* __restrict__ M, bool transM, double2 w, bool accumulate) {
-    count_flops(8.0 * (double)(L * nout * R) * nin);
+    count_flops_t<T>(8.0 * (double)(L * nout * R) * nin);
     if (transM || nin != nout || nin > (sizeof(T) == 16 ? 16 : 32)) {
         mode_prod_simple(out, in, L, nin, nout, R, M, transM, w, accumulate);
         return;
@@ -351,7 +359,7 @@ template <class T>
 __device__ void gram_acc(T* G, const T* __restrict__ X, const T* __restrict__ Y, const Shape& sh, int k, double2 w) {
     const int chi = sh.d[k];
     const int64_t L = sh.before(k), R = sh.after(k), O = L * R;
-    count_flops(8.0 * (double)O * chi * chi);
+    count_flops_t<T>(8.0 * (double)O * chi * chi);
     int OT = (kStageBytes / 2) / (chi * (int)sizeof(T));
     if (OT > 128) OT = 128;
     T* Xs = (T*)dyn_smem;            // [OT][chi]
@@ -542,7 +550,7 @@ __device__ void qr_mode(T* A, const Shape& sh, int k, double2* Wc, double2* Qc, 
         __syncthreads();
         if (threadIdx.x == 0) { x[j] = make_double2(beta, 0.0); sm.qskip[j] = 0; sm.qtau[j] = tau; }
         const double2 ctau = make_double2(tau.x, -tau.y);
-        count_flops(16.0 * (double)(m - j) * (n - j - 1) + 8.0 * (m - j));
+        count_flops_t<double2>(16.0 * (double)(m - j) * (n - j - 1) + 8.0 * (m - j));
         for (int c = j + 1 + warp; c < n; c += kWarps) {
             double2* y = Wc + (int64_t)c * m;
             double2 acc = make_double2(0.0, 0.0);
@@ -569,7 +577,7 @@ __device__ void qr_mode(T* A, const Shape& sh, int k, double2* Wc, double2* Qc, 
         if (sm.qskip[j]) continue;
         const double2 tau = sm.qtau[j];
         const double2* x = Wc + (int64_t)j * m;
-        count_flops(16.0 * (double)(m - j) * (n - j));
+        count_flops_t<double2>(16.0 * (double)(m - j) * (n - j));
         for (int c = j + warp; c < n; c += kWarps) {
             double2* y = Qc + (int64_t)c * m;
             double2 acc = make_double2(0.0, 0.0);
@@ -703,7 +711,7 @@ __device__ int krylov_once(TS* x, const Shape& sh, const TtnEntry* es, int ne, c
                     }
                 __syncthreads();
             }
-            count_flops(16.0 * (double)S * (j + 1));
+            count_flops_t<TB>(16.0 * (double)S * (j + 1));
             for (int64_t e = threadIdx.x; e < S; e += kThreads) {
                 TB acc = w[e];
                 for (int i = 0; i <= j; ++i) {
@@ -747,7 +755,7 @@ __device__ int krylov_once(TS* x, const Shape& sh, const TtnEntry* es, int ne, c
         if (!isfinite(err)) return -1;
         if (err <= tol || hnext == 0.0) {
             const double2 y0 = sm.y[0];
-            count_flops(8.0 * (double)S * mm);
+            count_flops_t<TB>(8.0 * (double)S * mm);
             for (int64_t e = threadIdx.x; e < S; e += kThreads) {
                 TB acc = czero<TB>();
                 for (int i = 1; i < mm; ++i) cfma(acc, cT<TB>(sm.y[i]), V[(int64_t)i * smax + e]);
@@ -885,7 +893,7 @@ __device__ void small_gemm(double2* C, const double2* A, const double2* B, int m
         }
         C[idx] = acc;
     }
-    count_flops(8.0 * m * k * n);
+    count_flops_t<double2>(8.0 * m * k * n);
     __syncthreads();
 }
 
@@ -1321,6 +1329,7 @@ __global__ void __launch_bounds__(kThreads, 2) program_kernel(const TtnInstance*
     const int nr = nrep < 0 ? in.nrep : nrep;
     if (threadIdx.x == 0) {
         s_flops = 0.0;
+        s_flops64 = 0.0;
         for (int i = 0; i < 8; ++i) s_sub[i] = 0;
         s_t0 = global_ns();
         s_stop = 0;
@@ -1345,7 +1354,10 @@ __global__ void __launch_bounds__(kThreads, 2) program_kernel(const TtnInstance*
             if (s_stop) break;
         }
     }
-    if (threadIdx.x == 0 && in.flops) atomicAdd(in.flops, s_flops);
+    if (threadIdx.x == 0 && in.flops) {
+        atomicAdd(in.flops, s_flops);
+        atomicAdd(in.flops + 1, s_flops64);
+    }
     if (threadIdx.x == 0 && in.op_cycles)
         for (int i = 0; i < 8; ++i) atomicAdd(&in.op_cycles[16 + i], s_sub[i]);
     if (threadIdx.x == 0 && rep_out) {
@@ -1362,7 +1374,7 @@ __global__ void __launch_bounds__(kThreads, 2) program_kernel(const TtnInstance*
 __global__ void __launch_bounds__(kThreads, 1) heff_kernel(const TtnEntry* es, int ne, const TtnSlot* slots, int D,
                                                            Shape sh, const double2* x, double2* y, double2* t1,
                                                            double2* t2, double2* t3) {
-    if (threadIdx.x == 0) s_flops = 0.0;
+    if (threadIdx.x == 0) { s_flops = 0.0; s_flops64 = 0.0; }
     __syncthreads();
     (void)D;
     heff_apply(y, x, t1, t2, t3, sh, es, ne, slots);

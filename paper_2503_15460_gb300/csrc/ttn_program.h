@@ -86,7 +86,7 @@ struct TtnInstance {
     int* status;            // device status word (0 = ok, else ttn_status code)
     int* steps_done;        // device step counter
     unsigned long long* stamps;  // optional per-step completion time stamps (ns)
-    double* flops;          // algorithmic flop counter (accumulated by block thread 0)
+    double* flops;          // algorithmic flop counters: [0] all, [1] the FP64 part (block thread 0)
     unsigned long long* op_cycles;  // SM clock cycles spent per op type (16 counters)
     double ktol;
     double qtol;            // QR rank threshold relative to ||M||_F

@@ -76,6 +76,7 @@ _sig = {
                         np.ctypeslib.ndpointer(dtype=np.uint64, flags="C_CONTIGUOUS"), C.c_int,
                         C.POINTER(C.c_int)], C.c_int),
     "ttn_device_bytes": ([_P, C.POINTER(C.c_size_t)], C.c_int),
+    "ttn_flop_counts": ([_P, C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
     "ttn_last_error": ([_P], C.c_char_p),
     "ttn_destroy": ([_P], None),
     "ttn_server_create": ([C.c_int, C.POINTER(ttn_server_opts), C.POINTER(_P)], C.c_int),
@@ -292,6 +293,12 @@ def ttn_step_stats(ctx, max_stamps=4096):
     n = C.c_int(0)
     _check(_lib.ttn_step_stats(ctx, C.byref(steps), C.byref(fl), st, int(max_stamps), C.byref(n)), ctx)
     return steps.value, fl.value, st[:n.value].copy()
+
+
+def ttn_flop_counts(ctx):
+    t, f = C.c_double(0.0), C.c_double(0.0)
+    _check(_lib.ttn_flop_counts(ctx, C.byref(t), C.byref(f)), ctx)
+    return t.value, f.value
 
 
 def ttn_set_stream(ctx, stream_handle: int):
