@@ -329,7 +329,7 @@ def run_reference(args, rank, world):
 # ---------------------------------------------------------------------------
 # serving stream (continuous batching through ttn_server)
 # ---------------------------------------------------------------------------
-SERVE_RANGES = dict(n_modes_range=(8, 128), d_range=(8, 20), chi_range=(4, 16), steps_range=(20, 80))
+SERVE_RANGES = dict(n_modes_range=(8, 64), d_range=(8, 20), chi_range=(4, 12), steps_range=(10, 40))
 
 
 def serve_workload_name(n):
@@ -394,27 +394,36 @@ def run_serving(args):
                 "launches": st["launches"], "peak_running": st["peak_running"],
                 "peak_bytes": st["peak_bytes"]}
 
+    def log(msg):
+        print(f"[serve] {msg}", file=sys.stderr, flush=True)
+
+    log(f"{len(probs)} requests, {total_steps} steps")
     burst = run(np.zeros(len(probs)))
+    log(f"burst: {burst['makespan_s']:.1f} s, {burst['steps_per_s']:.1f} steps/s")
     rate = 0.8 * burst["steps_per_s"] / (total_steps / len(probs))        # requests per second
     rng = np.random.default_rng(55)
     poisson_arr = np.cumsum(rng.exponential(1.0 / rate, len(probs)))
     poisson = run(poisson_arr)
     poisson["arrival_rate_per_s"] = rate
+    log(f"poisson: {poisson['makespan_s']:.1f} s, {poisson['steps_per_s']:.1f} steps/s")
 
-    # reference: one request at a time, complex128, on a sample
+    # reference: one request at a time, complex128, on a sample of requests
+    # and steps (the rate is steps per second of device work, one at a time)
     sample = list(range(min(args.serve_sample, len(probs))))
-    t = 0.0
+    t, sample_steps = 0.0, 0
     for i in sample:
         p = probs[i]
+        n = min(p.nsteps, args.serve_sample_steps)
         c = ttn.Context(p.tree, ttn.TTN_FP64)
         c.set_state(p.tensors)
         c.set_hamiltonian(p.H)
         t0 = time.perf_counter()
-        c.step(p.dt, p.nsteps)
+        c.step(p.dt, n)
         t += time.perf_counter() - t0
+        sample_steps += n
         c.close()
-    sample_steps = sum(probs[i].nsteps for i in sample)
     alone_rate = sample_steps / t
+    log(f"one at a time FP64: {alone_rate:.2f} steps/s over {sample_steps} steps")
     line = {
         "metric": "serving: aggregate TTN-TDVP steps/s, continuous batching (mixed) vs one request at a time (FP64)",
         "value": poisson["steps_per_s"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
@@ -423,8 +432,9 @@ def run_serving(args):
                    "arrivals": "Poisson at 80% of the burst capacity (seed 55)", "slice_ms": args.slice_ms},
         "poisson": poisson, "burst": burst,
         "one_at_a_time_fp64": {"value": alone_rate, "unit": UNIT,
-                               "sample": f"first {len(sample)} requests run alone with ttn_step, "
-                                         f"{sample_steps} steps; aggregate rate = steps / time"},
+                               "sample": f"first {len(sample)} requests run alone with ttn_step, at most "
+                                         f"{args.serve_sample_steps} steps each ({sample_steps} steps); "
+                                         f"rate = steps / time"},
         "speedup_vs_one_at_a_time_fp64": poisson["steps_per_s"] / alone_rate,
     }
     print(json.dumps(line), flush=True)
@@ -446,6 +456,7 @@ def main():
     ap.add_argument("--serve", action="store_true", help="run the serving stream instead (separate JSON line)")
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--serve-sample", type=int, default=8)
+    ap.add_argument("--serve-sample-steps", type=int, default=3)
     ap.add_argument("--slice-ms", type=float, default=20.0)
     args = ap.parse_args()
     if args.serve:
