@@ -209,7 +209,9 @@ __device__ void mode_prod_simple(T* __restrict__ out, const T* __restrict__ in, 
 
 // Square mode product with the matrix staged in shared memory and each
 // fibre in[l, :, r] held in registers: every thread produces all n outputs
-// of its fibre, reading the matrix rows as shared-memory broadcasts.
+// of its fibre, reading the matrix rows as shared-memory broadcasts.  Two
+// outputs are accumulated per pass, so four independent FMA chains hide
+// the FMA latency (one pass per output left half of the issue slots idle).
 template <class T, int MAXN>
 __device__ void mode_prod_tiled(T* __restrict__ out, const T* __restrict__ in, int64_t L, int n, int64_t R,
                                 const T* __restrict__ M, double2 w, bool accumulate) {
@@ -225,7 +227,26 @@ __device__ void mode_prod_tiled(T* __restrict__ out, const T* __restrict__ in, i
         T x[MAXN];
 #pragma unroll
         for (int m = 0; m < MAXN; ++m) x[m] = (m < n) ? src[m * R] : czero<T>();
-        for (int p = 0; p < n; ++p) {
+        int p = 0;
+        for (; p + 1 < n; p += 2) {
+            const T* row0 = Ms + p * n;
+            const T* row1 = row0 + n;
+            T a0 = czero<T>(), a1 = czero<T>();
+#pragma unroll
+            for (int m = 0; m < MAXN; ++m)
+                if (m < n) { cfma(a0, row0[m], x[m]); cfma(a1, row1[m], x[m]); }
+            T v0 = czero<T>(), v1 = czero<T>();
+            cfma(v0, wt, a0);
+            cfma(v1, wt, a1);
+            if (accumulate) {
+                T o0 = dst[p * R], o1 = dst[(p + 1) * R];
+                o0.x += v0.x; o0.y += v0.y; o1.x += v1.x; o1.y += v1.y;
+                dst[p * R] = o0; dst[(p + 1) * R] = o1;
+            } else {
+                dst[p * R] = v0; dst[(p + 1) * R] = v1;
+            }
+        }
+        if (p < n) {
             const T* row = Ms + p * n;
             T acc = czero<T>();
 #pragma unroll
