@@ -577,13 +577,16 @@ __device__ void qr_mode(T* A, const Shape& sh, int k, double2* Wc, double2* Qc, 
             double2 acc = make_double2(0.0, 0.0);
             for (int64_t i = j + lane; i < m; i += 32) {
                 double2 v = (i == j) ? make_double2(1.0, 0.0) : x[i];
-                acc = cadd(acc, cconjmul(v, y[i]));
+                cfmaconj(acc, v, y[i]);
             }
             acc = warp_sum(acc);
             const double2 f = cmul(ctau, acc);
+            const double2 nf = make_double2(-f.x, -f.y);
             for (int64_t i = j + lane; i < m; i += 32) {
                 double2 v = (i == j) ? make_double2(1.0, 0.0) : x[i];
-                y[i] = csub(y[i], cmul(v, f));
+                double2 yi = y[i];
+                cfma(yi, v, nf);
+                y[i] = yi;
             }
         }
         __syncthreads();
@@ -604,13 +607,16 @@ __device__ void qr_mode(T* A, const Shape& sh, int k, double2* Wc, double2* Qc, 
             double2 acc = make_double2(0.0, 0.0);
             for (int64_t i = j + lane; i < m; i += 32) {
                 double2 v = (i == j) ? make_double2(1.0, 0.0) : x[i];
-                acc = cadd(acc, cconjmul(v, y[i]));
+                cfmaconj(acc, v, y[i]);
             }
             acc = warp_sum(acc);
             const double2 f = cmul(tau, acc);
+            const double2 nf = make_double2(-f.x, -f.y);
             for (int64_t i = j + lane; i < m; i += 32) {
                 double2 v = (i == j) ? make_double2(1.0, 0.0) : x[i];
-                y[i] = csub(y[i], cmul(v, f));
+                double2 yi = y[i];
+                cfma(yi, v, nf);
+                y[i] = yi;
             }
         }
         __syncthreads();
@@ -733,7 +739,20 @@ __device__ int krylov_once(TS* x, const Shape& sh, const TtnEntry* es, int ne, c
                 __syncthreads();
             }
             count_flops_t<TB>(16.0 * (double)S * (j + 1));
-            for (int64_t e = threadIdx.x; e < S; e += kThreads) {
+            int64_t e = threadIdx.x;
+            for (; e + kThreads < S; e += 2 * kThreads) {
+                TB a0 = w[e], a1 = w[e + kThreads];
+                for (int i = 0; i <= j; ++i) {
+                    const double2 h = sm.dots[i];
+                    const TB nh = cT<TB>(make_double2(-h.x, -h.y));
+                    const TB* Vi = V + (int64_t)i * smax + e;
+                    cfma(a0, nh, Vi[0]);
+                    cfma(a1, nh, Vi[kThreads]);
+                }
+                w[e] = a0;
+                w[e + kThreads] = a1;
+            }
+            if (e < S) {
                 TB acc = w[e];
                 for (int i = 0; i <= j; ++i) {
                     const double2 h = sm.dots[i];
