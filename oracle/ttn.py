@@ -323,6 +323,48 @@ class TTN:
             self.sweep_Sstar(0, dt / 2.0)
             self.t_elapsed += dt
 
+    # -- one-site ground-state sweep (tree DMRG) --------------------------------
+    # The paper names DMRG beside the time evolution (Sec. I, Sec. II.C): the
+    # same environments, effective Hamiltonian and gauge moves, with each node
+    # tensor replaced by the lowest eigenvector of its effective Hamiltonian
+    # instead of being propagated.
+    def heff_lowest(self, z):
+        """Lowest eigenpair of H_eff^z (Hermitian): dense eigh of the matrix
+        formed column by column for small nodes, ARPACK Lanczos (started from
+        the current tensor) otherwise."""
+        shape = self.A[z].shape
+        n = int(np.prod(shape))
+        if n <= 600:
+            M = np.empty((n, n), dtype=np.complex128)
+            for i in range(n):
+                e = np.zeros(n, dtype=np.complex128)
+                e[i] = 1.0
+                M[:, i] = self.heff(z, e.reshape(shape)).ravel()
+            w, V = np.linalg.eigh(M)
+            return float(w[0]), V[:, 0].reshape(shape)
+        import scipy.sparse.linalg as spla
+        op = spla.LinearOperator((n, n), dtype=np.complex128,
+                                 matvec=lambda v: self.heff(z, v.reshape(shape)).ravel())
+        w, V = spla.eigsh(op, k=1, which="SA", tol=1e-14, v0=self.A[z].ravel().copy())
+        v = V[:, 0]
+        return float(w[0]), (v / np.linalg.norm(v)).reshape(shape)
+
+    def sweep_ground(self, z):
+        """Visiting order of S: centre to each child by QR, recursion, centre
+        back (no bond step), then A^z <- lowest eigenvector of H_eff^z.
+        Returns the eigenvalue found at z."""
+        for k, c in enumerate(self.ch[z]):
+            self._move_down(z, k)
+            self.sweep_ground(c)
+            C = self._move_up(z, k)
+            self.A[z] = mode_product(C, self.A[z], k)
+        e, self.A[z] = self.heff_lowest(z)
+        return e
+
+    def ground_state(self, nsweeps: int = 1):
+        """Energies (root eigenvalue) after each of nsweeps sweeps."""
+        return [self.sweep_ground(0) for _ in range(nsweeps)]
+
     # -- observables -----------------------------------------------------------
     def shf_gram(self):
         """G^z[m', m] = <Psi_m'^z | Psi_m^z> for every node with the centre at the

@@ -498,3 +498,55 @@ def test_adaptive_expansion_improves_accuracy():
     e_adapt = np.abs(np.concatenate(adapt.populations(p.obs_leaves)) - want).max()
     assert max(adapt.t.bond_dim[1:]) > 2
     assert e_adapt < 0.25 * e_fixed
+
+
+# ---------------------------------------------------------------------------
+# one-site ground-state sweeps (tree DMRG)
+# ---------------------------------------------------------------------------
+def test_ground_state_full_bonds_is_exact():
+    """At full bond dimension the root's effective Hamiltonian is the whole
+    Hamiltonian in a rotated basis, so one sweep ends at the exact ground
+    energy (dense diagonalisation of the 512-dim spin-boson H)."""
+    p = W.config_c1(full_bonds=True, d=4)
+    e0 = np.linalg.eigvalsh(exact.full_hamiltonian(p.tree, p.H).toarray())[0]
+    ref = TTN(p.tree, p.H, p.tensors)
+    es = ref.ground_state(2)
+    assert abs(es[-1] - e0) <= 1e-10 * max(1.0, abs(e0))
+    assert abs(ref.energy().real - e0) <= 1e-10 * max(1.0, abs(e0))
+
+
+def test_ground_state_variational_and_monotone():
+    """Truncated bonds (chi = 4): energies never increase from sweep to sweep,
+    stay above the exact ground energy (sparse Lanczos on the 8192-dim H),
+    and equal <Psi|H|Psi> of the normalised state."""
+    import scipy.sparse.linalg as spla
+    p = W.config_c1()
+    Hs = exact.full_hamiltonian(p.tree, p.H)
+    e0 = spla.eigsh(Hs, k=1, which="SA", tol=1e-12, v0=np.ones(Hs.shape[0]))[0][0]
+    rng = np.random.default_rng(3)
+    ref = TTN(p.tree, p.H, random_canonical(p.tree, rng))
+    es = ref.ground_state(4)
+    for a, b in zip(es, es[1:]):
+        assert b <= a + 1e-12
+    assert es[-1] >= e0 - 1e-10
+    assert es[-1] - e0 <= 0.05 * abs(e0)        # a good variational estimate already
+    n2 = ref.norm2()
+    assert abs(n2 - 1.0) <= 1e-12
+    assert abs(ref.energy().real - es[-1]) <= 1e-10
+
+
+def test_ground_state_uncoupled_is_product_of_local_minima():
+    """Without couplings the ground energy is the sum of the local minima."""
+    t = small_tree()
+    rng = np.random.default_rng(5)
+    H = W.SOP(hermitian=True)
+    want = 0.0
+    for l in t.leaves():
+        d = int(t.phys_dim[l])
+        X = rng.normal(size=(d, d)) + 1j * rng.normal(size=(d, d))
+        h = X + X.conj().T
+        H.add(1.0, (l, h))
+        want += np.linalg.eigvalsh(h)[0]
+    ref = TTN(t, H, random_canonical(t, rng))
+    es = ref.ground_state(2)
+    assert abs(es[-1] - want) <= 1e-10 * max(1.0, abs(want))
