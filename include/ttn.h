@@ -177,6 +177,22 @@ ttn_status ttn_set_sop_hamiltonian(ttn_ctx* ctx, int n_terms, const ttn_c128* co
  * (defaults).  Blocks until the device work has finished. */
 ttn_status ttn_step(ttn_ctx* ctx, double dt, int nsteps, const ttn_step_opts* opts);
 
+/* Ground state by one-site tree DMRG sweeps (the paper names DMRG beside
+ * the time evolution, Sec. I and Sec. II.C; same environments, effective
+ * Hamiltonian and gauge moves as ttn_step).  One sweep visits the nodes in
+ * the order of the step's forward sweep S: centre moved to each child by
+ * QR, recursion, centre moved back, then the node tensor replaced by the
+ * normalised lowest eigenvector of its effective Hamiltonian (restarted
+ * Lanczos with full reorthogonalisation; residual below 1e-12 relative in
+ * TTN_FP64, 1e-7 in TTN_MIXED).  Bond dimensions stay fixed, so the state
+ * only explores the span of its current single-particle functions
+ * (occupied and unoccupied).  energies[i] (may be NULL) receives the
+ * root's eigenvalue after sweep i: the energy <Psi|H|Psi> of the
+ * normalised state, non-increasing from sweep to sweep up to the
+ * tolerance.  Hermitian Hamiltonians only (TTN_E_INVALID otherwise);
+ * TTN_E_NOCONV if an eigen-solve fails to converge in 200 restarts. */
+ttn_status ttn_ground_state(ttn_ctx* ctx, int nsweeps, double* energies);
+
 /* Advance n independent contexts (same precision) by nsteps steps of dt in
  * one device launch, one thread block per context; the stream of ctxs[0]
  * is used.  Contexts may have different trees and Hamiltonians.  Fixed bond

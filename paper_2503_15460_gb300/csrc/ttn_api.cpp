@@ -120,7 +120,7 @@ OpsLayout ops_layout(const ttn::Plan& P) {
     for (auto& s : P.slots) L.slot_bytes = std::max(L.slot_bytes, (size_t)s.off + (size_t)s.rows * s.cols * P.esz);
     L.slot_bytes = al(L.slot_bytes);
     size_t n_ops_total = P.init_prog.ops.size() + P.step_prog.ops.size() + P.norm_energy_prog.ops.size() +
-                         P.spawn_prog.ops.size();
+                         P.spawn_prog.ops.size() + P.ground_prog.ops.size();
     for (auto& p : P.rdm_prog) n_ops_total += p.ops.size();
     for (auto& p : P.vac_prog) n_ops_total += p.ops.size();
     for (auto& p : P.to_root_prog) n_ops_total += p.ops.size();
@@ -168,7 +168,7 @@ void free_ops(ttn_ctx* c) {
     c->ops_bytes = 0;
     c->d_slots = nullptr;
     c->d_entries = nullptr;
-    c->init_p = c->step_p = c->ne_p = c->spawn_p = DevProgram();
+    c->init_p = c->step_p = c->ne_p = c->spawn_p = c->ground_p = DevProgram();
     c->rdm_p.clear(); c->vac_p.clear(); c->to_root_p.clear();
     c->d_inst = nullptr;
 }
@@ -222,6 +222,7 @@ ttn_status upload_ops(ttn_ctx* c) {
     c->step_p = link(P.step_prog);
     c->ne_p = link(P.norm_energy_prog);
     c->spawn_p = link(P.spawn_prog);
+    c->ground_p = link(P.ground_prog);
     for (auto& p : P.rdm_prog) c->rdm_p.push_back(link(p));
     for (auto& p : P.vac_prog) c->vac_p.push_back(link(p));
     for (auto& p : P.to_root_prog) c->to_root_p.push_back(link(p));
@@ -590,6 +591,24 @@ ttn_status ttn_step(ttn_ctx* c, double dt, int nsteps, const ttn_step_opts* opts
         if (s) return s;
         s = run_program(c, c->step_p, dt, 1);
         if (s) return s;
+    }
+    return TTN_OK;
+}
+
+ttn_status ttn_ground_state(ttn_ctx* c, int nsweeps, double* energies) {
+    ttn_status u = usable(c); if (u) return u;
+    if (!c->has_h) return fail(c, TTN_E_STATE, "no Hamiltonian set");
+    if (!c->ham.hermitian) return fail(c, TTN_E_INVALID, "ground-state sweeps need a Hermitian Hamiltonian");
+    if (nsweeps < 0) return fail(c, TTN_E_INVALID, "nsweeps must be >= 0");
+    u = ready(c); if (u) return u;
+    for (int i = 0; i < nsweeps; ++i) {
+        ttn_status s = run_program(c, c->ground_p, 0.0, 1);
+        if (s) return s;
+        if (energies) {
+            CK(cudaMemcpyAsync(&energies[i], c->d_state + c->plan.scal_off + 64, sizeof(double),
+                               cudaMemcpyDeviceToHost, c->stream), "energy copy");
+            CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+        }
     }
     return TTN_OK;
 }

@@ -46,7 +46,7 @@ struct ttn_ctx {
     size_t ops_bytes = 0;
     TtnSlot* d_slots = nullptr;
     TtnEntry* d_entries = nullptr;
-    ttn::DevProgram init_p, step_p, ne_p, spawn_p;
+    ttn::DevProgram init_p, step_p, ne_p, spawn_p, ground_p;
     std::vector<ttn::DevProgram> rdm_p, vac_p, to_root_p;
     TtnInstance* d_inst = nullptr; // staging for single-instance launches
     TtnInstance* d_batch = nullptr;

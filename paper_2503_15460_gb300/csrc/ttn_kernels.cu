@@ -695,10 +695,34 @@ __device__ void small_expm(Smem& sm, int m, double tau, bool band) {
 // Returns 1 when converged (x updated), 0 when kmax was reached, -1 on a
 // non-finite norm.
 // ---------------------------------------------------------------------------
+__device__ void jacobi_eigh(double2* A, double2* Vm, int n, Smem& sm);
+
+// Lowest Ritz pair of the m x m Hermitian tridiagonal Lanczos matrix in
+// sm.H (all threads): eigen-decomposition by cyclic Jacobi in the stage
+// buffer, eigenvector to sm.y[0..m), eigenvalue to sm.u[0].x.
+__device__ void lowest_ritz(Smem& sm, int m) {
+    double2* T = (double2*)(dyn_smem + 16384);
+    double2* Vm = (double2*)(dyn_smem + 32768);
+    for (int i = threadIdx.x; i < m * m; i += kThreads) {
+        const int r = i / m, c = i - (i / m) * m;
+        T[i] = sm.H[r * TTN_KMAX + c];
+    }
+    __syncthreads();
+    jacobi_eigh(T, Vm, m, sm);
+    if (threadIdx.x == 0) {
+        int imin = 0;
+        for (int i = 1; i < m; ++i)
+            if (T[i * m + i].x < T[imin * m + imin].x) imin = i;
+        for (int i = 0; i < m; ++i) sm.y[i] = Vm[i * m + imin];
+        sm.u[0] = make_double2(T[imin * m + imin].x, 0.0);
+    }
+    __syncthreads();
+}
+
 template <class TS, class TB>
 __device__ int krylov_once(TS* x, const Shape& sh, const TtnEntry* es, int ne, const TtnSlot* slots,
                            double tau, int herm, double tol, int kmax, TB* V, int64_t smax, TB* t1, TB* t2,
-                           TB* t3, Smem& sm) {
+                           TB* t3, Smem& sm, int ground = 0) {
     double logbound = 0.0;          // log(|tau|^m prod h_{i+1,i} / m!)
     const int64_t S = sh.size();
     double2 nb = make_double2(0.0, 0.0);
@@ -780,8 +804,38 @@ __device__ int krylov_once(TS* x, const Shape& sh, const TtnEntry* es, int ne, c
         // estimate; the small exponential is evaluated only once this bound is
         // within 1e4 of the tolerance (always at kmax and on breakdown).
         logbound += log(fmax(hnext, 1e-300)) + log(fabs(tau) + 1e-300) - log((double)mm);
-        const bool near = logbound <= log(1e4 * tol) || j == kmax - 1 || hnext == 0.0 || (j & 3) == 3;
+        const bool near = ground ? ((j & 1) == 1 || j == kmax - 1 || hnext == 0.0)
+                                 : (logbound <= log(1e4 * tol) || j == kmax - 1 || hnext == 0.0 || (j & 3) == 3);
         if (!near) {
+            const double inv = 1.0 / hnext;
+            for (int64_t e = threadIdx.x; e < S; e += kThreads) w[e] = cT<TB>(cscale(cd(w[e]), inv));
+            __syncthreads();
+            continue;
+        }
+        if (ground) {
+            // lowest Ritz pair; Lanczos residual |h_{m+1,m} y_m| against tol * max(1, |theta|)
+            lowest_ritz(sm, mm);
+            const double theta = sm.u[0].x;
+            const double res = hnext * sqrt(cabs2(sm.y[j]));
+            if (!isfinite(res) || !isfinite(theta)) return -1;
+            const bool conv = res <= tol * fmax(1.0, fabs(theta)) || hnext == 0.0;
+            if (conv || j == kmax - 1) {
+                // x <- sum_i y_i V_i with V_0 = x / beta0 taken from x itself, then renormalised
+                const double2 y0 = cscale(sm.y[0], 1.0 / beta0);
+                count_flops_t<TB>(8.0 * (double)S * mm);
+                for (int64_t e = threadIdx.x; e < S; e += kThreads) {
+                    TB acc = czero<TB>();
+                    for (int i = 1; i < mm; ++i) cfma(acc, cT<TB>(sm.y[i]), V[(int64_t)i * smax + e]);
+                    x[e] = cT<TS>(cadd(cmul(y0, cd(x[e])), cd(acc)));
+                }
+                __syncthreads();
+                double2 nx = make_double2(0.0, 0.0);
+                for (int64_t e = threadIdx.x; e < S; e += kThreads) nx.x += cabs2(cd(x[e]));
+                const double inv = 1.0 / sqrt(block_sum(nx, sm).x);
+                for (int64_t e = threadIdx.x; e < S; e += kThreads) x[e] = cT<TS>(cscale(cd(x[e]), inv));
+                __syncthreads();
+                return conv ? 1 : 0;
+            }
             const double inv = 1.0 / hnext;
             for (int64_t e = threadIdx.x; e < S; e += kThreads) w[e] = cT<TB>(cscale(cd(w[e]), inv));
             __syncthreads();
@@ -828,6 +882,23 @@ __device__ int krylov_expm(TS* x, const Shape& sh, const TtnEntry* es, int ne, c
         }
     }
     return 1;
+}
+
+// Lowest eigenpair of a Hermitian H_eff by restarted Lanczos (restart from
+// the current Ritz vector after kmax steps).  Returns 1 and the eigenvalue
+// on convergence, 0 otherwise.
+template <class TS, class TB>
+__device__ int krylov_ground(TS* x, const Shape& sh, const TtnEntry* es, int ne, const TtnSlot* slots, double tol,
+                             int kmax, TB* V, int64_t smax, TB* t1, TB* t2, TB* t3, Smem& sm, double* theta) {
+    for (int r = 0; r < 200; ++r) {
+        const int s = krylov_once(x, sh, es, ne, slots, 0.0, 1, tol, kmax, V, smax, t1, t2, t3, sm, 1);
+        if (s < 0) return 0;
+        if (s > 0) {
+            *theta = sm.u[0].x;
+            return 1;
+        }
+    }
+    return 0;
 }
 
 template <class TB, class TS>
@@ -1285,6 +1356,17 @@ __device__ void run_op(const TtnOp& op, const TtnInstance& in, double dt, Smem& 
         const int ok = krylov_expm((TS*)op.a, sh, es, op.ne, in.slots, op.tau_coef * dt, op.hermitian, in.ktol,
                                    in.kmax, V, in.smax, t1, t2, t3, sm);
         if (!ok && threadIdx.x == 0) atomicExch(in.status, 4);   // TTN_E_NOCONV
+        __syncthreads();
+        break;
+    }
+    case TTN_OP_EIGEN: {
+        // residual tolerance: FP64 rounding allows ~1e-12 relative; an FP32 Krylov basis ~1e-7
+        const double etol = sizeof(TB) == 16 ? fmax(in.ktol, 1e-12) : fmax(in.ktol, 1e-7);
+        double theta = 0.0;
+        const int ok = krylov_ground((TS*)op.a, sh, es, op.ne, in.slots, etol, in.kmax, V, in.smax, t1, t2, t3, sm,
+                                     &theta);
+        if (!ok && threadIdx.x == 0) atomicExch(in.status, 4);   // TTN_E_NOCONV
+        if (ok && threadIdx.x == 0 && op.out) op.out[0] = theta;
         __syncthreads();
         break;
     }

@@ -768,6 +768,34 @@ struct Builder {
         }
     }
 
+    // One-site ground-state sweep (tree DMRG; the paper lists it beside the
+    // time evolution, Sec. I and Sec. II.C): the visiting order of S with
+    // the centre moved by QR and every node replaced by the lowest
+    // eigenvector of its effective Hamiltonian; no bond step.  The root's
+    // eigenvalue (the energy of the normalised state) lands in the scalar
+    // area at byte offset 64.
+    void emit_eigen_node(Program& pr, int z) {
+        emit_combos(pr, heff_combo[z]);
+        OpSpec s = tensor_op(TTN_OP_EIGEN, z, 0);
+        s.op.e0 = heff_rng[z].first; s.op.ne = heff_rng[z].second;
+        s.op.hermitian = 1;
+        s.out_off = p.scal_off + 64;
+        pr.ops.push_back(s);
+    }
+    void emit_ground(Program& pr, int z) {
+        for (size_t k = 0; k < t.ch[z].size(); ++k) {
+            int c = t.ch[z][k];
+            emit_qr_down(pr, z, (int)k);
+            emit_absorb_child(pr, c);
+            emit_env_down(pr, z, (int)k);
+            emit_ground(pr, c);
+            emit_qr_up(pr, c);
+            emit_env_up(pr, c);
+            emit_absorb_parent(pr, z, (int)k);
+        }
+        emit_eigen_node(pr, z);
+    }
+
     // Subspace-expansion pass (paper Sec. II.D): the sweep order of S with
     // the centre moved by QR but no time evolution; the SPAWN op of a bond
     // stops the program when it accepts new functions.
@@ -961,6 +989,7 @@ std::string make_plan(const Tree& t, const Hamiltonian* h, int precision, Plan& 
         b.emit_S(p.step_prog, 0);
         b.emit_Sstar(p.step_prog, 0);
         b.emit_spawn_visit(p.spawn_prog, 0);
+        if (h->hermitian) b.emit_ground(p.ground_prog, 0);
         b.make_to_root();
         // spawn workspace: K = (distinct up channels of a bond's terms) x bond dimension
         int kmax = 0;

@@ -78,6 +78,7 @@ struct Plan {
     Program init_prog;               // environment build after a state / Hamiltonian change
     Program step_prog;               // one time step
     Program spawn_prog;              // subspace-expansion pass (stops at the first bond that grows)
+    Program ground_prog;             // one ground-state sweep (one-site tree DMRG), Hermitian H only
     std::vector<Program> to_root_prog;   // per node: move the orthogonality centre from it to the root
     int64_t spawn_out_off = 0;       // bytes: spawn result area
     int64_t spawn_out_bytes = 0;

@@ -32,7 +32,8 @@ enum TtnOpType : int {
     TTN_OP_TRACE = 9,        // out scalar <- sum_ab slot0[a,b] * slot1[b,a]   (k = dim)
     TTN_OP_CONTRACT_VEC = 10,// a' <- contraction of tensor a with matrices on modes (vacuum projection)
     TTN_OP_STEP_END = 11,    // end of one time step (timestamp, step counter)
-    TTN_OP_SPAWN = 12        // subspace expansion test of the bond to child k (centre at a)
+    TTN_OP_SPAWN = 12,       // subspace expansion test of the bond to child k (centre at a)
+    TTN_OP_EIGEN = 13        // a <- lowest eigenvector of H (entries, Hermitian), normalised; out <- eigenvalue
 };
 
 // Status word value left by a SPAWN op that accepted new single-particle

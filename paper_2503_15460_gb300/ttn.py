@@ -61,6 +61,7 @@ _sig = {
     "ttn_set_sop_hamiltonian": ([_P, C.c_int, _C128, _I32, _I32, _C128, _I64, C.c_int], C.c_int),
     "ttn_step": ([_P, C.c_double, C.c_int, C.POINTER(ttn_step_opts)], C.c_int),
     "ttn_step_batch": ([C.POINTER(_P), C.c_int, C.c_double, C.c_int, C.POINTER(ttn_step_opts)], C.c_int),
+    "ttn_ground_state": ([_P, C.c_int, _F64], C.c_int),
     "ttn_reduced_density": ([_P, C.c_int, _C128], C.c_int),
     "ttn_expect": ([_P, C.c_int, _I32, _C128, _I64, _C128], C.c_int),
     "ttn_norm_energy": ([_P, C.POINTER(C.c_double), _C128], C.c_int),
@@ -200,6 +201,12 @@ def ttn_step(ctx, dt, nsteps=1, opts=None):
     _check(_lib.ttn_step(ctx, float(dt), int(nsteps), _opts(opts)), ctx)
 
 
+def ttn_ground_state(ctx, nsweeps):
+    e = np.zeros(max(1, int(nsweeps)), dtype=np.float64)
+    _check(_lib.ttn_ground_state(ctx, int(nsweeps), e), ctx)
+    return e[:int(nsweeps)].copy()
+
+
 def ttn_step_batch(ctxs, dt, nsteps=1, opts=None):
     arr = (_P * len(ctxs))(*[c.value if isinstance(c, _P) else c for c in ctxs])
     st = _lib.ttn_step_batch(arr, len(ctxs), float(dt), int(nsteps), _opts(opts))
@@ -250,7 +257,7 @@ def ttn_bond_dims(ctx, n_nodes):
 
 
 OP_NAMES = {1: "qr_down", 2: "qr_up", 3: "absorb_child", 4: "absorb_parent", 5: "env", 6: "combo",
-            7: "evolve", 8: "dot", 9: "trace", 10: "contract_vec", 11: "step_end",
+            7: "evolve", 8: "dot", 9: "trace", 10: "contract_vec", 11: "step_end", 12: "spawn", 13: "eigen",
             16: "in:heff", 17: "in:gram_schmidt", 18: "in:small_expm", 19: "in:gram", 20: "in:convert"}
 
 
@@ -445,6 +452,9 @@ class Context:
 
     def step(self, dt, nsteps=1, opts=None):
         ttn_step(self.h, dt, nsteps, opts)
+
+    def ground_state(self, nsweeps=1):
+        return ttn_ground_state(self.h, nsweeps)
 
     def rdm(self, leaf):
         return ttn_reduced_density(self.h, leaf, int(self.tree.phys_dim[leaf]))
