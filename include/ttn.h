@@ -291,7 +291,8 @@ ttn_status ttn_flop_counts(ttn_ctx* ctx, double* total, double* fp64);
 /* SM clock cycles the context's device programs spent per operation type,
  * cycles[32] (index: 1 QR towards a child, 2 QR towards the parent,
  * 3/4 bond absorption into child/parent, 5 environment builds, 6 operator
- * combinations, 7 Krylov exponentials, 8-10 observables, 11 step end;
+ * combinations, 7 Krylov exponentials, 8-10 observables, 11 step end,
+ * 12 subspace-expansion tests, 13 ground-state eigen-solves;
  * inside those: 16 effective-Hamiltonian products, 17 Gram-Schmidt,
  * 18 small projected exponentials, 19 Gram contractions, 20 conversions). */
 ttn_status ttn_op_cycles(ttn_ctx* ctx, uint64_t* cycles);
