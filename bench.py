@@ -67,6 +67,28 @@ def workload_name(batch):
             f"local dims 10..30), batch of {batch} seeded instances, dt={DT}")
 
 
+def rank_seed0(batch, rank):
+    """First seed of a rank's instances: ranks draw disjoint seed ranges
+    (weak scaling: every rank holds `batch` independent instances)."""
+    return 2 + rank * batch
+
+
+def max_over_ranks(x, world, device):
+    """The slowest rank's value (no-op for one rank)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(batch, world, steps, seconds):
+    """Whole-job instance-steps per second."""
+    return batch * world * steps / seconds
+
+
 def make_problems(batch, seed0):
     import workloads as W
     return [W.config_c2(seed=seed0 + i) for i in range(batch)]
@@ -132,7 +154,7 @@ def run_ours(args, rank, world, local_rank):
     ttn.ttn_set_device(local_rank)
     stream = torch.cuda.Stream()
     batch = args.batch
-    probs = make_problems(batch, 2 + rank * batch)
+    probs = make_problems(batch, rank_seed0(batch, rank))
 
     def make_ctxs(precision, subset=None):
         out = []
@@ -167,12 +189,7 @@ def run_ours(args, rank, world, local_rank):
         ev1.synchronize()
     torch.cuda.synchronize()
     barrier()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world, "cuda")
     clocks = clk.summary()
     fl1 = np.sum([ttn.ttn_flop_counts(h) for h in handles], axis=0)
     flops_per_step, flops64_per_step = (fl1 - fl0) / args.steps
@@ -181,7 +198,7 @@ def run_ours(args, rank, world, local_rank):
         _, _, st = ttn.ttn_step_stats(h, args.steps + 1)
         if len(st) >= 2:
             lat.extend(np.diff(st.astype(np.float64)) / 1e6)
-    value = batch * world * args.steps / (ms / 1e3)
+    value = aggregate_rate(batch, world, args.steps, ms / 1e3)
 
     # ---- plain FP64 on the same batch ----------------------------------------
     fp64 = None
@@ -197,8 +214,8 @@ def run_ours(args, rank, world, local_rank):
                 ttn.ttn_step_batch(h64, DT, 1)
             e1.record(stream)
         e1.synchronize()
-        ms64 = e0.elapsed_time(e1)
-        fp64 = {"value": batch * world * args.fp64_steps / (ms64 / 1e3), "unit": UNIT,
+        ms64 = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
+        fp64 = {"value": aggregate_rate(batch, world, args.fp64_steps, ms64 / 1e3), "unit": UNIT,
                 "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps}
         # population error mixed vs FP64 after the same number of steps on a subset
         nchk = min(args.check_instances, batch)
@@ -238,14 +255,8 @@ def run_ours(args, rank, world, local_rank):
             d2h += sum(x.nbytes for x in pops) * 2      # complex d x d read back per leaf
         torch.cuda.synchronize()
         t1 = time.perf_counter()
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([t1 - t0], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
-        else:
-            el = t1 - t0
-        e2e = {"value": batch * world * args.steps / el, "unit": UNIT,
+        el = max_over_ranks(t1 - t0, world, "cuda")
+        e2e = {"value": aggregate_rate(batch, world, args.steps, el), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(d2h / args.steps),
                "includes": "context creation, state and Hamiltonian upload, K steps, population read-back"}
         for c in ce:
