@@ -323,6 +323,14 @@ class TTN:
             self.sweep_Sstar(0, dt / 2.0)
             self.t_elapsed += dt
 
+    def set_coefficients(self, coeffs):
+        """Time-dependent SOP coefficients c_r(t) (Sec. II.E: the bath
+        mappings make them time dependent): the environments here are per
+        term and carry no coefficient, so replacing c_r is all there is."""
+        import dataclasses
+        assert len(coeffs) == self.H.n_terms
+        self.H = dataclasses.replace(self.H, coeffs=[complex(c) for c in coeffs])
+
     # -- one-site ground-state sweep (tree DMRG) --------------------------------
     # The paper names DMRG beside the time evolution (Sec. I, Sec. II.C): the
     # same environments, effective Hamiltonian and gauge moves, with each node
