@@ -173,6 +173,17 @@ ttn_status ttn_set_sop_hamiltonian(ttn_ctx* ctx, int n_terms, const ttn_c128* co
                                    const ttn_c128* factor_mats, const int64_t* factor_mat_off,
                                    int hermitian);
 
+/* Time-dependent coefficients c_r(t) (the paper's interaction-picture and
+ * chain mappings of a bath make the SOP coefficients time dependent,
+ * Sec. II.E): replace the coefficients of the Hamiltonian last set by
+ * ttn_set_sop_hamiltonian, keeping its factors (n_terms must be the same;
+ * coefficients may become or stop being zero).  Everything that depends on
+ * them -- pre-summed local operators, term weights, environments -- is
+ * rebuilt; the state is unchanged.  Holding c(t + dt/2) over a step of
+ * ttn_step(dt) (midpoint rule) keeps the step second-order accurate for
+ * smooth c(t).  The cost is one host re-plan and one environment build. */
+ttn_status ttn_set_coefficients(ttn_ctx* ctx, int n_terms, const ttn_c128* coeff);
+
 /* Advance by nsteps steps of length dt (Sec. II.C).  opts may be NULL
  * (defaults).  Blocks until the device work has finished. */
 ttn_status ttn_step(ttn_ctx* ctx, double dt, int nsteps, const ttn_step_opts* opts);

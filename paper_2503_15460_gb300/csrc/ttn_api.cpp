@@ -547,6 +547,22 @@ ttn_status ttn_set_sop_hamiltonian(ttn_ctx* c, int n_terms, const ttn_c128* coef
     ttn::Plan P;
     msg = ttn::make_plan(c->tree, &h, c->precision, P);
     if (!msg.empty()) return fail(c, TTN_E_INVALID, msg);
+    {
+        const int nf = n_terms > 0 && term_ptr ? term_ptr[n_terms] : 0;
+        int64_t nm = 0;
+        for (int f = 0; f < nf; ++f) {
+            const int64_t d = c->tree.phys[factor_leaf[f]];
+            nm = std::max<int64_t>(nm, factor_mat_off[f] + d * d);
+        }
+        std::vector<cplx> sc((const cplx*)coeff, (const cplx*)coeff + n_terms);
+        std::vector<int> sp(term_ptr, term_ptr + (n_terms > 0 ? n_terms + 1 : 0));
+        std::vector<int> sl(factor_leaf ? factor_leaf : sp.data(), factor_leaf ? factor_leaf + nf : sp.data());
+        std::vector<cplx> sm_((const cplx*)factor_mats, (const cplx*)factor_mats + (nf > 0 ? nm : 0));
+        std::vector<int64_t> so(factor_mat_off ? factor_mat_off : nullptr, factor_mat_off ? factor_mat_off + nf : nullptr);
+        c->sop_coeff.swap(sc); c->sop_ptr.swap(sp); c->sop_leaf.swap(sl);
+        c->sop_mats.swap(sm_); c->sop_off.swap(so);
+        c->sop_herm = hermitian;
+    }
     if (!c->resident) {
         c->ham = h;
         c->has_h = true;
@@ -570,6 +586,23 @@ ttn_status ttn_set_sop_hamiltonian(ttn_ctx* c, int n_terms, const ttn_c128* coef
     ttn_status s = upload_ops(c);
     if (s) { c->failed = true; return s; }
     return run_program(c, c->init_p, 0.0, 1);
+}
+
+ttn_status ttn_set_coefficients(ttn_ctx* c, int n_terms, const ttn_c128* coeff) {
+    ttn_status u = usable(c); if (u) return u;
+    if (!c->has_h) return fail(c, TTN_E_STATE, "no Hamiltonian set");
+    if (n_terms != (int)c->sop_coeff.size() || (n_terms > 0 && !coeff))
+        return fail(c, TTN_E_INVALID, "n_terms differs from the Hamiltonian's term count");
+    for (int r = 0; r < n_terms; ++r)
+        if (!std::isfinite(coeff[r].re) || !std::isfinite(coeff[r].im)) return fail(c, TTN_E_INVALID, "non-finite coefficient");
+    // replay the set-up with the stored factors (local copies: the call replaces them)
+    const std::vector<int> ptr = c->sop_ptr, leaf = c->sop_leaf;
+    const std::vector<cplx> mats = c->sop_mats;
+    const std::vector<int64_t> off = c->sop_off;
+    return ttn_set_sop_hamiltonian(c, n_terms, coeff, ptr.empty() ? nullptr : ptr.data(),
+                                   leaf.empty() ? nullptr : leaf.data(),
+                                   mats.empty() ? nullptr : (const ttn_c128*)mats.data(),
+                                   off.empty() ? nullptr : off.data(), c->sop_herm);
 }
 
 ttn_status ttn_step(ttn_ctx* c, double dt, int nsteps, const ttn_step_opts* opts) {

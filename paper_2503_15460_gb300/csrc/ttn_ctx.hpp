@@ -54,6 +54,12 @@ struct ttn_ctx {
     double ktol = 0.0;
     double qtol = 0.0;
     int kmax = TTN_KMAX;
+    // The SOP as last given to ttn_set_sop_hamiltonian (ttn_set_coefficients
+    // replays it with new coefficients).
+    std::vector<ttn::cplx> sop_coeff, sop_mats;
+    std::vector<int> sop_ptr, sop_leaf;
+    std::vector<int64_t> sop_off;
+    int sop_herm = 1;
     int64_t steps_total = 0;
     int64_t spawned = 0;            // single-particle functions added by expansion
 };

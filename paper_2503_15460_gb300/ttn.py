@@ -62,6 +62,7 @@ _sig = {
     "ttn_step": ([_P, C.c_double, C.c_int, C.POINTER(ttn_step_opts)], C.c_int),
     "ttn_step_batch": ([C.POINTER(_P), C.c_int, C.c_double, C.c_int, C.POINTER(ttn_step_opts)], C.c_int),
     "ttn_ground_state": ([_P, C.c_int, _F64], C.c_int),
+    "ttn_set_coefficients": ([_P, C.c_int, _C128], C.c_int),
     "ttn_reduced_density": ([_P, C.c_int, _C128], C.c_int),
     "ttn_expect": ([_P, C.c_int, _I32, _C128, _I64, _C128], C.c_int),
     "ttn_norm_energy": ([_P, C.POINTER(C.c_double), _C128], C.c_int),
@@ -199,6 +200,11 @@ def _opts(opts):
 
 def ttn_step(ctx, dt, nsteps=1, opts=None):
     _check(_lib.ttn_step(ctx, float(dt), int(nsteps), _opts(opts)), ctx)
+
+
+def ttn_set_coefficients(ctx, coeff):
+    coeff = np.ascontiguousarray(coeff, dtype=np.complex128)
+    _check(_lib.ttn_set_coefficients(ctx, len(coeff), coeff if coeff.size else np.zeros(1, np.complex128)), ctx)
 
 
 def ttn_ground_state(ctx, nsweeps):
@@ -452,6 +458,9 @@ class Context:
 
     def step(self, dt, nsteps=1, opts=None):
         ttn_step(self.h, dt, nsteps, opts)
+
+    def set_coefficients(self, coeff):
+        ttn_set_coefficients(self.h, coeff)
 
     def ground_state(self, nsweeps=1):
         return ttn_ground_state(self.h, nsweeps)

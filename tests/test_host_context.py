@@ -76,3 +76,22 @@ def test_request_generator_shapes():
         assert p.nsteps == r["steps"]
         assert p.dt == (0.05 if r["kind"] == "sb" else 0.1)
         assert len(p.obs_leaves) == r["n_modes"] + 1
+
+
+def test_set_coefficients_on_host_context(lib):
+    p = W.config_c1(eps=1.0)
+    c = host_ctx(lib, p)
+    fp = c.footprint()
+    coeff = np.array(p.H.coeffs, dtype=np.complex128)
+    coeff[0] *= 0.5
+    c.set_coefficients(coeff)                       # same factors: accepted, no device work
+    assert c.device_bytes() == 0 and c.footprint() == fp
+    with pytest.raises(lib.TTNError) as e:
+        c.set_coefficients(coeff[:-1])
+    assert e.value.status == lib.TTN_E_INVALID
+    bad = coeff.copy()
+    bad[1] = np.nan
+    with pytest.raises(lib.TTNError) as e:
+        c.set_coefficients(bad)
+    assert e.value.status == lib.TTN_E_INVALID
+    c.close()
