@@ -184,6 +184,23 @@ ttn_status ttn_set_sop_hamiltonian(ttn_ctx* ctx, int n_terms, const ttn_c128* co
  * smooth c(t).  The cost is one host re-plan and one environment build. */
 ttn_status ttn_set_coefficients(ttn_ctx* ctx, int n_terms, const ttn_c128* coeff);
 
+/* Checkpoint / resume (the paper has no counterpart: long propagations
+ * are resumed from saved states).  ttn_save writes the tree (with the
+ * current bond dimensions, which subspace expansion may have grown), the
+ * step and flop counters, the Hamiltonian as last given (coefficients,
+ * factors, matrices, hermitian flag) and every node tensor (complex128,
+ * centre at the root) into buf, a self-describing byte stream of *len
+ * bytes; with buf == NULL it only stores the required size in *len, and a
+ * too small *len gives TTN_E_INVALID with the size in *len.  ttn_load
+ * replaces the tree, state, Hamiltonian and counters of ctx by those of a
+ * checkpoint, keeping ctx's precision and residency (a resident context is
+ * re-materialised, environments rebuilt).  Device time stamps and cycle
+ * counters are not saved.  A stream that is not a checkpoint, is
+ * truncated or inconsistent returns TTN_E_INVALID and leaves ctx
+ * unchanged.  Resuming gives bit-identical results to not stopping. */
+ttn_status ttn_save(ttn_ctx* ctx, void* buf, size_t* len);
+ttn_status ttn_load(ttn_ctx* ctx, const void* buf, size_t len);
+
 /* Advance by nsteps steps of length dt (Sec. II.C).  opts may be NULL
  * (defaults).  Blocks until the device work has finished. */
 ttn_status ttn_step(ttn_ctx* ctx, double dt, int nsteps, const ttn_step_opts* opts);
@@ -232,6 +249,13 @@ ttn_status ttn_vacuum_projection(ttn_ctx* ctx, int keep_leaf, ttn_c128* out);
 /* Copy all node tensors to the host, in the layout of ttn_set_state;
  * offsets (n_nodes+1 entries) receives the layout. */
 ttn_status ttn_get_state(ttn_ctx* ctx, ttn_c128* tensors, int64_t* offsets);
+
+/* The context's tree as it is now (ttn_load or subspace expansion may have
+ * changed it since ttn_create): *n_nodes, and, for each non-NULL array of
+ * n_nodes entries, parent (root: -1), phys_dim (0 for interior nodes) and
+ * the current bond dimension to the parent (root: 1).  Call with NULL
+ * arrays first to learn n_nodes. */
+ttn_status ttn_tree(const ttn_ctx* ctx, int* n_nodes, int* parent, int* phys_dim, int* bond_dim);
 
 /* Bond dimension of every node to its parent (root: 1), out[n_nodes]. */
 ttn_status ttn_bond_dims(ttn_ctx* ctx, int* out);

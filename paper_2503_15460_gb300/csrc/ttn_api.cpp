@@ -478,6 +478,41 @@ ttn_status ttn::ctx_evict(ttn_ctx* c) {
     return TTN_OK;
 }
 
+namespace {
+
+// Checkpoint byte stream: little helpers over a growing buffer / a cursor.
+struct Writer {
+    std::vector<char> b;
+    template <class T> void put(const T& v) { const char* p = (const char*)&v; b.insert(b.end(), p, p + sizeof(T)); }
+    template <class T> void put_vec(const std::vector<T>& v) {
+        put<int64_t>((int64_t)v.size());
+        const char* p = (const char*)v.data();
+        b.insert(b.end(), p, p + v.size() * sizeof(T));
+    }
+};
+struct Reader {
+    const char* p;
+    size_t left;
+    bool ok = true;
+    template <class T> T get() {
+        T v{};
+        if (left < sizeof(T)) { ok = false; return v; }
+        std::memcpy(&v, p, sizeof(T)); p += sizeof(T); left -= sizeof(T);
+        return v;
+    }
+    template <class T> std::vector<T> get_vec(int64_t max_n) {
+        const int64_t n = get<int64_t>();
+        std::vector<T> v;
+        if (!ok || n < 0 || n > max_n || (size_t)n * sizeof(T) > left) { ok = false; return v; }
+        v.resize((size_t)n);
+        std::memcpy(v.data(), p, (size_t)n * sizeof(T)); p += n * sizeof(T); left -= n * sizeof(T);
+        return v;
+    }
+};
+const uint32_t kCkptMagic = 0x314E5454u;   // "TTN1"
+
+}  // namespace
+
 extern "C" {
 
 ttn_status ttn_create(int n_nodes, const int* parent, const int* phys_dim, const int* bond_dim, int precision,
@@ -586,6 +621,116 @@ ttn_status ttn_set_sop_hamiltonian(ttn_ctx* c, int n_terms, const ttn_c128* coef
     ttn_status s = upload_ops(c);
     if (s) { c->failed = true; return s; }
     return run_program(c, c->init_p, 0.0, 1);
+}
+
+ttn_status ttn_save(ttn_ctx* c, void* buf, size_t* len) {
+    ttn_status u = usable(c); if (u) return u;
+    if (!len) return fail(c, TTN_E_INVALID, "len is NULL");
+    std::vector<std::vector<cplx>> A;
+    int64_t steps = c->saved_steps;
+    double flops[2] = {c->saved_flops, c->saved_flops64};
+    if (c->resident) {
+        ttn_status s = download_state(c, A);
+        if (s) return s;
+        int st = 0;
+        CK(cudaMemcpyAsync(&st, c->d_state + c->plan.steps_off, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "counter copy");
+        CK(cudaMemcpyAsync(flops, c->d_state + c->plan.flops_off, sizeof(flops), cudaMemcpyDeviceToHost, c->stream), "counter copy");
+        CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+        steps = st;
+    } else {
+        A = c->host_A;
+    }
+    Writer w;
+    w.put<uint32_t>(kCkptMagic);
+    w.put<int32_t>(c->precision);
+    w.put_vec(c->tree.parent);
+    w.put_vec(c->tree.phys);
+    std::vector<int> bond(c->tree.n);
+    for (int z = 0; z < c->tree.n; ++z) bond[z] = z == 0 ? 1 : c->tree.bond[z];
+    w.put_vec(bond);
+    w.put<int64_t>(steps);
+    w.put<double>(flops[0]);
+    w.put<double>(flops[1]);
+    w.put<int32_t>(c->has_h ? 1 : 0);
+    w.put<int32_t>(c->sop_herm);
+    w.put_vec(c->sop_coeff);
+    w.put_vec(c->sop_ptr);
+    w.put_vec(c->sop_leaf);
+    w.put_vec(c->sop_off);
+    w.put_vec(c->sop_mats);
+    for (int z = 0; z < c->tree.n; ++z) w.put_vec(A[z]);
+    const size_t need = w.b.size();
+    if (!buf) { *len = need; return TTN_OK; }
+    if (*len < need) { *len = need; return fail(c, TTN_E_INVALID, "buffer too small for the checkpoint"); }
+    std::memcpy(buf, w.b.data(), need);
+    *len = need;
+    return TTN_OK;
+}
+
+ttn_status ttn_load(ttn_ctx* c, const void* buf, size_t len) {
+    ttn_status u = usable(c); if (u) return u;
+    if (!buf) return fail(c, TTN_E_INVALID, "buf is NULL");
+    Reader r{(const char*)buf, len};
+    const int64_t big = (int64_t)1 << 40;
+    if (r.get<uint32_t>() != kCkptMagic || !r.ok) return fail(c, TTN_E_INVALID, "not a libttn checkpoint");
+    r.get<int32_t>();                                // precision of the saving context (informational)
+    std::vector<int> parent = r.get_vec<int>(65535), phys = r.get_vec<int>(65535), bond = r.get_vec<int>(65535);
+    const int64_t steps = r.get<int64_t>();
+    const double f0 = r.get<double>(), f1 = r.get<double>();
+    const int has_h = r.get<int32_t>(), herm = r.get<int32_t>();
+    std::vector<cplx> coeff = r.get_vec<cplx>(big);
+    std::vector<int> ptr = r.get_vec<int>(big), leaf = r.get_vec<int>(big);
+    std::vector<int64_t> off = r.get_vec<int64_t>(big);
+    std::vector<cplx> mats = r.get_vec<cplx>(big);
+    if (!r.ok || parent.size() != phys.size() || parent.size() != bond.size() || parent.empty())
+        return fail(c, TTN_E_INVALID, "truncated or inconsistent checkpoint");
+    ttn::Tree t;
+    std::string msg = ttn::build_tree((int)parent.size(), parent.data(), phys.data(), bond.data(), t);
+    if (!msg.empty()) return fail(c, TTN_E_INVALID, "checkpoint tree: " + msg);
+    std::vector<std::vector<cplx>> A(t.n);
+    for (int z = 0; z < t.n; ++z) {
+        A[z] = r.get_vec<cplx>(big);
+        if (!r.ok || (int64_t)A[z].size() != t.size[z]) return fail(c, TTN_E_INVALID, "checkpoint tensor " + std::to_string(z) + " has the wrong size");
+    }
+    if (has_h) {
+        const int nt = (int)coeff.size();
+        if ((int)ptr.size() != nt + 1 || ptr[nt] != (int)leaf.size() || leaf.size() != off.size())
+            return fail(c, TTN_E_INVALID, "inconsistent Hamiltonian in the checkpoint");
+        ttn::Hamiltonian h;
+        msg = ttn::build_hamiltonian(t, nt, coeff.data(), ptr.data(), leaf.empty() ? nullptr : leaf.data(),
+                                     mats.empty() ? nullptr : mats.data(), off.empty() ? nullptr : off.data(), herm, h);
+        if (!msg.empty()) return fail(c, TTN_E_INVALID, "checkpoint Hamiltonian: " + msg);
+    }
+    // everything validated: replace the context's contents, keeping its residency
+    const bool was_resident = c->resident;
+    if (c->resident) {
+        free_ops(c);
+        dev_free(c, c->d_state);
+        c->d_state = nullptr;
+        c->state_bytes = 0;
+        if (c->d_batch) cudaFree(c->d_batch);
+        c->d_batch = nullptr;
+        c->batch_cap = 0;
+        c->resident = false;
+    }
+    c->tree = t;
+    c->has_h = false;
+    c->ham = ttn::Hamiltonian();
+    ttn::make_plan(c->tree, nullptr, c->precision, c->plan);
+    c->host_A.swap(A);
+    c->saved_steps = steps;
+    c->saved_flops = f0;
+    c->saved_flops64 = f1;
+    c->sop_coeff.clear(); c->sop_ptr.clear(); c->sop_leaf.clear(); c->sop_off.clear(); c->sop_mats.clear();
+    if (has_h) {
+        ttn_status s = ttn_set_sop_hamiltonian(c, (int)coeff.size(), (const ttn_c128*)coeff.data(), ptr.data(),
+                                               leaf.empty() ? nullptr : leaf.data(),
+                                               mats.empty() ? nullptr : (const ttn_c128*)mats.data(),
+                                               off.empty() ? nullptr : off.data(), herm);
+        if (s) return s;
+    }
+    if (was_resident) return ready(c);
+    return TTN_OK;
 }
 
 ttn_status ttn_set_coefficients(ttn_ctx* c, int n_terms, const ttn_c128* coeff) {
@@ -771,6 +916,17 @@ ttn_status ttn_get_state(ttn_ctx* c, ttn_c128* tensors, int64_t* offsets) {
         o += c->tree.size[z];
     }
     offsets[c->tree.n] = o;
+    return TTN_OK;
+}
+
+ttn_status ttn_tree(const ttn_ctx* c, int* n_nodes, int* parent, int* phys_dim, int* bond_dim) {
+    if (!c || !n_nodes) return TTN_E_INVALID;
+    *n_nodes = c->tree.n;
+    for (int z = 0; z < c->tree.n; ++z) {
+        if (parent) parent[z] = c->tree.parent[z];
+        if (phys_dim) phys_dim[z] = c->tree.phys[z];
+        if (bond_dim) bond_dim[z] = z == 0 ? 1 : c->tree.bond[z];
+    }
     return TTN_OK;
 }
 

@@ -63,12 +63,15 @@ _sig = {
     "ttn_step_batch": ([C.POINTER(_P), C.c_int, C.c_double, C.c_int, C.POINTER(ttn_step_opts)], C.c_int),
     "ttn_ground_state": ([_P, C.c_int, _F64], C.c_int),
     "ttn_set_coefficients": ([_P, C.c_int, _C128], C.c_int),
+    "ttn_save": ([_P, C.c_void_p, C.POINTER(C.c_size_t)], C.c_int),
+    "ttn_load": ([_P, C.c_void_p, C.c_size_t], C.c_int),
     "ttn_reduced_density": ([_P, C.c_int, _C128], C.c_int),
     "ttn_expect": ([_P, C.c_int, _I32, _C128, _I64, _C128], C.c_int),
     "ttn_norm_energy": ([_P, C.POINTER(C.c_double), _C128], C.c_int),
     "ttn_vacuum_projection": ([_P, C.c_int, _C128], C.c_int),
     "ttn_get_state": ([_P, _C128, _I64], C.c_int),
     "ttn_bond_dims": ([_P, _I32], C.c_int),
+    "ttn_tree": ([_P, C.POINTER(C.c_int), C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "ttn_set_stream": ([_P, _P], C.c_int),
     "ttn_set_device": ([C.c_int], C.c_int),
     "ttn_heff_apply": ([_P, C.c_int, _I32, C.c_int, _C128, _I32, C.c_int, C.POINTER(_P), _P, _P], C.c_int),
@@ -207,6 +210,19 @@ def ttn_set_coefficients(ctx, coeff):
     _check(_lib.ttn_set_coefficients(ctx, len(coeff), coeff if coeff.size else np.zeros(1, np.complex128)), ctx)
 
 
+def ttn_save(ctx) -> bytes:
+    n = C.c_size_t(0)
+    _check(_lib.ttn_save(ctx, None, C.byref(n)), ctx)
+    buf = C.create_string_buffer(n.value)
+    _check(_lib.ttn_save(ctx, buf, C.byref(n)), ctx)
+    return buf.raw[:n.value]
+
+
+def ttn_load(ctx, data: bytes):
+    buf = C.create_string_buffer(bytes(data), len(data))
+    _check(_lib.ttn_load(ctx, buf, len(data)), ctx)
+
+
 def ttn_ground_state(ctx, nsweeps):
     e = np.zeros(max(1, int(nsweeps)), dtype=np.float64)
     _check(_lib.ttn_ground_state(ctx, int(nsweeps), e), ctx)
@@ -256,10 +272,18 @@ def ttn_get_state(ctx, sizes):
     return [flat[offs[i]:offs[i + 1]] for i in range(len(sizes))]
 
 
-def ttn_bond_dims(ctx, n_nodes):
-    out = np.zeros(n_nodes, dtype=np.int32)
-    _check(_lib.ttn_bond_dims(ctx, out), ctx)
-    return out
+def ttn_tree(ctx):
+    """(parent, phys_dim, bond_dim) of the context's current tree."""
+    n = C.c_int(0)
+    _check(_lib.ttn_tree(ctx, C.byref(n), None, None, None), ctx)
+    par, phys, bond = (np.zeros(n.value, dtype=np.int32) for _ in range(3))
+    _check(_lib.ttn_tree(ctx, C.byref(n), par.ctypes.data, phys.ctypes.data, bond.ctypes.data), ctx)
+    return par, phys, bond
+
+
+def ttn_bond_dims(ctx, n_nodes=None):
+    """Bond dimensions (root: 1); the length is the library's node count."""
+    return ttn_tree(ctx)[2]
 
 
 OP_NAMES = {1: "qr_down", 2: "qr_up", 3: "absorb_child", 4: "absorb_parent", 5: "env", 6: "combo",
@@ -428,6 +452,26 @@ class Server:
 # ---------------------------------------------------------------------------
 # convenience wrapper around a context handle
 # ---------------------------------------------------------------------------
+class TreeView:
+    """Tree shape as the library reports it (parent, phys_dim, bond_dim)."""
+
+    def __init__(self, parent, phys_dim, bond_dim):
+        self.parent, self.phys_dim, self.bond_dim = parent, phys_dim, bond_dim
+
+    @property
+    def n(self):
+        return len(self.parent)
+
+    def children(self, z):
+        return [c for c in range(z + 1, self.n) if self.parent[c] == z]
+
+    def is_leaf(self, z):
+        return self.phys_dim[z] > 0
+
+    def leaves(self):
+        return [z for z in range(self.n) if self.phys_dim[z] > 0]
+
+
 class Context:
     """Owns one ttn_ctx.  ``tree`` is a workloads.Tree (parent/phys_dim/bond_dim)."""
 
@@ -461,6 +505,15 @@ class Context:
 
     def set_coefficients(self, coeff):
         ttn_set_coefficients(self.h, coeff)
+
+    def save(self) -> bytes:
+        return ttn_save(self.h)
+
+    def load(self, data: bytes):
+        """Replace tree, state and Hamiltonian by a checkpoint's; the tree
+        view becomes the checkpoint's tree."""
+        ttn_load(self.h, data)
+        self.tree = TreeView(*ttn_tree(self.h))
 
     def ground_state(self, nsweeps=1):
         return ttn_ground_state(self.h, nsweeps)

@@ -95,3 +95,34 @@ def test_set_coefficients_on_host_context(lib):
         c.set_coefficients(bad)
     assert e.value.status == lib.TTN_E_INVALID
     c.close()
+
+
+def test_checkpoint_round_trip_on_host(lib):
+    p = W.config_c2(bonds=(6, 4, 3, 2), d_range=(4, 6))
+    a = host_ctx(lib, p)
+    blob = a.save()
+    # load into a context built on another tree: tree, state and H are replaced
+    q = W.config_c1()
+    b = lib.Context(q.tree, lib.TTN_MIXED, on_host=True)
+    b.load(blob)
+    assert b.device_bytes() == 0
+    assert b.footprint() == a.footprint()
+    assert np.array_equal(b.bond_dims(), a.bond_dims())
+    assert np.array_equal(b.tree.parent, p.tree.parent)     # tree view follows the load
+    for x, y in zip(a.get_state(), b.get_state()):
+        assert np.array_equal(x, y)
+    assert b.save() == blob
+    a.close(); b.close()
+
+
+def test_checkpoint_rejects_bad_streams(lib):
+    p = W.config_c1()
+    a = host_ctx(lib, p)
+    blob = a.save()
+    for bad in (b"not a checkpoint", blob[: len(blob) // 2], b"\x00" * 64):
+        with pytest.raises(lib.TTNError) as e:
+            a.load(bad)
+        assert e.value.status == lib.TTN_E_INVALID
+    # the context is unchanged after the failed loads
+    assert a.save() == blob
+    a.close()
