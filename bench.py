@@ -62,9 +62,20 @@ def measured_traffic(batch):
     return rec["dram_bytes_per_instance_step"] * batch
 
 
-def workload_name(batch):
+def workload_name(batch, workload="vibronic"):
+    if workload == "heom":
+        return (f"HEOM spin-boson as a TTN: 16 exponentials (Drude-Lorentz + 15 Matsubara), depth 10 "
+                f"(32 modes of dim 11), system leaf dim 4, balanced binary tree (65 nodes), chi 24, Arnoldi; "
+                f"batch of {batch} instances sweeping the reorganisation energy lambda, dt={WORKLOAD_DT[workload]}")
+    if workload == "spinboson300":
+        return (f"spin-boson, 1 spin + 300 Ohmic modes (wc 5, orthogonal-polynomial bath on [0, 50]), d 20, "
+                f"balanced binary tree (601 nodes), fixed chi 8; batch of {batch} instances sweeping alpha "
+                f"in [0.1, 0.5], dt={WORKLOAD_DT[workload]}")
     return (f"vibronic 2 states x 24 modes, ML tree depth 4 (46 nodes, bonds 24/16/12/8, "
             f"local dims 10..30), batch of {batch} seeded instances, dt={DT}")
+
+
+WORKLOAD_DT = {"vibronic": DT, "heom": 0.015, "spinboson300": 0.01}
 
 
 def rank_seed0(batch, rank):
@@ -89,8 +100,25 @@ def aggregate_rate(batch, world, steps, seconds):
     return batch * world * steps / seconds
 
 
-def make_problems(batch, seed0):
+def make_problems(batch, seed0, workload="vibronic"):
+    """Instances of a workload; instance index i = seed0 + i - 2 picks the
+    seed (vibronic) or the swept parameter (heom: lambda, spinboson300:
+    alpha)."""
     import workloads as W
+    if workload == "heom":
+        return [W.config_c4(lam=0.05 + 0.0005 * (seed0 - 2 + i)) for i in range(batch)]
+    if workload == "spinboson300":
+        # alpha only scales the couplings (g ~ sqrt(alpha)): discretise once
+        import dataclasses
+        base = W.config_c3(alpha=0.1)
+        out = []
+        for i in range(batch):
+            a = 0.1 + 0.4 * (((seed0 - 2 + i) * 0.618034) % 1.0)
+            sc = np.sqrt(a / 0.1)
+            H = dataclasses.replace(base.H, coeffs=[c * sc if len(f) == 2 else c
+                                                    for c, f in zip(base.H.coeffs, base.H.factors)])
+            out.append(dataclasses.replace(base, H=H, name=f"c3_alpha{a:.4f}"))
+        return out
     return [W.config_c2(seed=seed0 + i) for i in range(batch)]
 
 
@@ -154,7 +182,8 @@ def run_ours(args, rank, world, local_rank):
     ttn.ttn_set_device(local_rank)
     stream = torch.cuda.Stream()
     batch = args.batch
-    probs = make_problems(batch, rank_seed0(batch, rank))
+    DT = WORKLOAD_DT[args.workload]
+    probs = make_problems(batch, rank_seed0(batch, rank), args.workload)
 
     def make_ctxs(precision, subset=None):
         out = []
@@ -174,6 +203,7 @@ def run_ours(args, rank, world, local_rank):
     # ---- mixed precision, batched: the headline ------------------------------
     ctxs = make_ctxs(ttn.TTN_MIXED)
     handles = [c.h for c in ctxs]
+    batch_bytes = sum(ttn.ttn_device_bytes(h) for h in handles)
     for _ in range(args.warmup):
         ttn.ttn_step_batch(handles, DT, 1)
     fl0 = np.sum([ttn.ttn_flop_counts(h) for h in handles], axis=0)
@@ -265,7 +295,7 @@ def run_ours(args, rank, world, local_rank):
     for c in ctxs:
         c.close()
     return dict(ms=ms, value=value, flops_per_step=float(flops_per_step), flops64_per_step=float(flops64_per_step),
-                lat=lat, clocks=clocks, fp64=fp64, e2e=e2e)
+                lat=lat, clocks=clocks, fp64=fp64, e2e=e2e, batch_bytes=batch_bytes)
 
 
 def alu_roofline(flops, flops64, seconds, traffic):
@@ -464,6 +494,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=1)
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu", dest="cpu", action="store_false")
+    ap.add_argument("--workload", default="vibronic", choices=sorted(WORKLOAD_DT),
+                    help="vibronic (the headline), heom or spinboson300 (batched parameter sweeps)")
     ap.add_argument("--serve", action="store_true", help="run the serving stream instead (separate JSON line)")
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--serve-sample", type=int, default=8)
@@ -472,6 +504,8 @@ def main():
     args = ap.parse_args()
     if args.serve:
         return run_serving(args)
+    if args.workload != "vibronic":
+        args.e2e = args.cpu = False      # those legs are defined on the headline workload
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -490,9 +524,9 @@ def main():
             "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64 bulk / f64 state", "data": "synthetic",
-            "config": {"workload": workload_name(args.batch), "global_batch": args.batch * world,
+            "config": {"workload": workload_name(args.batch, args.workload), "global_batch": args.batch * world,
                        "instances_per_gpu": args.batch, "precision": "mixed",
-                       "l2": "inputs larger than L2 (per-instance working set ~30 MB x batch)",
+                       "l2": f"inputs larger than L2: the batch holds {r['batch_bytes'] / 1e9:.1f} GB on the device",
                        "parallelism": f"replicas x{world}, one thread block per instance"},
             "p50_step_latency_ms": float(np.percentile(lat, 50)) if lat else None,
             "p99_step_latency_ms": float(np.percentile(lat, 99)) if lat else None,
@@ -500,7 +534,7 @@ def main():
             "speedup_vs_fp64": (r["value"] / r["fp64"]["value"]) if r["fp64"] else None,
             "gpu_launches": args.steps,
             "roofline": alu_roofline(r["flops_per_step"], r["flops64_per_step"], r["ms"] / args.steps / 1e3,
-                                     measured_traffic(args.batch)),
+                                     measured_traffic(args.batch) if args.workload == "vibronic" else None),
             "clocks": r["clocks"],
             "e2e": r["e2e"],
         }
