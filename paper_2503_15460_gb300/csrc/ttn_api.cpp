@@ -700,6 +700,9 @@ ttn_status ttn_load(ttn_ctx* c, const void* buf, size_t len) {
         msg = ttn::build_hamiltonian(t, nt, coeff.data(), ptr.data(), leaf.empty() ? nullptr : leaf.data(),
                                      mats.empty() ? nullptr : mats.data(), off.empty() ? nullptr : off.data(), herm, h);
         if (!msg.empty()) return fail(c, TTN_E_INVALID, "checkpoint Hamiltonian: " + msg);
+        ttn::Plan probe;                             // plan now, so nothing fails after ctx is modified
+        msg = ttn::make_plan(t, &h, c->precision, probe);
+        if (!msg.empty()) return fail(c, TTN_E_INVALID, "checkpoint Hamiltonian: " + msg);
     }
     // everything validated: replace the context's contents, keeping its residency
     const bool was_resident = c->resident;

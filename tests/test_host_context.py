@@ -126,3 +126,13 @@ def test_checkpoint_rejects_bad_streams(lib):
     # the context is unchanged after the failed loads
     assert a.save() == blob
     a.close()
+
+
+def test_tree_query_follows_the_context(lib):
+    p = W.config_c2(bonds=(6, 4, 3, 2), d_range=(4, 6))
+    c = host_ctx(lib, p)
+    parent, phys, bond = lib.ttn_tree(c.h)
+    assert np.array_equal(parent, p.tree.parent)
+    assert np.array_equal(phys, p.tree.phys_dim)
+    assert np.array_equal(bond[1:], p.tree.bond_dim[1:]) and bond[0] == 1
+    c.close()
