@@ -610,3 +610,33 @@ def test_constant_coefficients_change_nothing():
         b.step(p.dt)
     for x, y in zip(a.A, b.A):
         assert np.array_equal(x, y)
+
+
+def test_ground_eigensolver_branches_agree():
+    """heff_lowest uses ARPACK above 600 elements: on such a node it gives
+    the lowest eigenpair of the dense H_eff formed column by column."""
+    p = W.config_c2(bonds=(8, 6, 4, 3), d_range=(4, 6))
+    ref = TTN(p.tree, p.H, random_canonical(p.tree, np.random.default_rng(8)))
+    sizes = [a.size for a in ref.A]
+    z = next(i for i, n in enumerate(sizes) if 600 < n <= 5000)
+    # bring the centre to z by one partial sweep: the root's children first
+    path = []
+    u = z
+    while u != 0:
+        path.append(u)
+        u = p.tree.parent[u]
+    for c in reversed(path):
+        par = p.tree.parent[c]
+        ref._move_down(par, ref.ch[par].index(c))
+    e, v = ref.heff_lowest(z)
+    shape = ref.A[z].shape
+    n = ref.A[z].size
+    M = np.empty((n, n), dtype=np.complex128)
+    for i in range(n):
+        x = np.zeros(n, dtype=np.complex128)
+        x[i] = 1.0
+        M[:, i] = ref.heff(z, x.reshape(shape)).ravel()
+    w, V = np.linalg.eigh(M)
+    assert abs(e - w[0]) <= 1e-10 * max(1.0, abs(w[0]))
+    assert abs(abs(np.vdot(V[:, 0], v.ravel())) - 1.0) <= 1e-8
+    assert w[1] - w[0] > 1e-6                     # non-degenerate, so the vector is unique
