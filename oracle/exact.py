@@ -36,11 +36,14 @@ def propagate_eigh(Hd: np.ndarray, psi0: np.ndarray, times):
 
 
 def propagate_sparse(Hs, psi0: np.ndarray, times):
-    """psi(t) = exp(-i H t) psi0 via scipy's expm_multiply (any H)."""
-    times = np.asarray(times, dtype=np.float64)
-    out = spla.expm_multiply(-1j * Hs, psi0, start=float(times[0]), stop=float(times[-1]),
-                             num=len(times), endpoint=True)
-    return [out[i] for i in range(len(times))]
+    """psi(t_i) = exp(-i H t_i) psi0 for increasing times t_i >= 0 (any H),
+    by scipy's expm_multiply over each interval in turn."""
+    out, psi, t_prev = [], np.asarray(psi0, dtype=np.complex128), 0.0
+    for t in times:
+        psi = spla.expm_multiply(-1j * (float(t) - t_prev) * Hs, psi)
+        out.append(psi)
+        t_prev = float(t)
+    return out
 
 
 def leaf_reduced_density(psi: np.ndarray, dims, pos: int) -> np.ndarray:

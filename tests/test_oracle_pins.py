@@ -640,3 +640,14 @@ def test_ground_eigensolver_branches_agree():
     assert abs(e - w[0]) <= 1e-10 * max(1.0, abs(w[0]))
     assert abs(abs(np.vdot(V[:, 0], v.ravel())) - 1.0) <= 1e-8
     assert w[1] - w[0] > 1e-6                     # non-degenerate, so the vector is unique
+
+
+def test_sparse_propagation_matches_eigh_at_uneven_times():
+    p = W.config_c1(full_bonds=True, d=4)
+    Hs = exact.full_hamiltonian(p.tree, p.H)
+    psi0 = full_state(p.tree, p.tensors)
+    times = [0.1, 0.35, 1.0, 1.05]
+    a = exact.propagate_sparse(Hs, psi0, times)
+    b = exact.propagate_eigh(Hs.toarray(), psi0, times)
+    for x, y in zip(a, b):
+        assert np.linalg.norm(x - y) <= 1e-10
