@@ -651,3 +651,35 @@ def test_sparse_propagation_matches_eigh_at_uneven_times():
     b = exact.propagate_eigh(Hs.toarray(), psi0, times)
     for x, y in zip(a, b):
         assert np.linalg.norm(x - y) <= 1e-10
+
+
+def test_vibronic_sop_is_the_model_formula():
+    """The shared vibronic generator against its formula written out with
+    Kronecker products: sum w_i (n_i + 1/2) - delta sz + sum kappa_i^s |s><s| Q_i
+    + sum gamma_j^s |s><s| Q_j^2 + sum lam_j sx Q_j, Q = (a + a^+)/sqrt 2."""
+    t = W.build_tree(("node", 1, [("leaf", 2, 2, "el"), ("leaf", 3, 3, "m0"), ("leaf", 4, 4, "m1")]))
+    el, m0, m1 = (t.leaf_of_label(x) for x in ("el", "m0", "m1"))
+    d = [3, 4]
+    rng = np.random.default_rng(12)
+    omega = rng.uniform(0.05, 0.5, 2)
+    kappa = rng.normal(0, 0.05, (2, 2))
+    gq = rng.normal(0, 0.01, (1, 2))
+    lam = rng.normal(0, 0.05, 1)
+    H = W.vibronic_sop(el, [m0, m1], d, omega, kappa, gq, [1], lam, [0], 0.1)
+    got = exact.full_hamiltonian(t, H).toarray()
+
+    def Q(n):
+        a = np.diag(np.sqrt(np.arange(1, n)), 1)
+        return (a + a.T) / np.sqrt(2.0)
+    I2, I3, I4 = np.eye(2), np.eye(3), np.eye(4)
+    P = [np.diag([1.0, 0.0]), np.diag([0.0, 1.0])]
+    sz, sx = np.diag([1.0, -1.0]), np.array([[0.0, 1.0], [1.0, 0.0]])
+    k3 = lambda A, B, C: np.kron(np.kron(A, B), C)
+    want = (omega[0] * k3(I2, np.diag(np.arange(3) + 0.5), I4)
+            + omega[1] * k3(I2, I3, np.diag(np.arange(4) + 0.5))
+            - 0.1 * k3(sz, I3, I4))
+    for s in range(2):
+        want = want + kappa[0, s] * k3(P[s], Q(3), I4) + kappa[1, s] * k3(P[s], I3, Q(4))
+        want = want + gq[0, s] * k3(P[s], I3, Q(4) @ Q(4))
+    want = want + lam[0] * k3(sx, Q(3), I4)
+    assert np.abs(got - want).max() <= 1e-14
