@@ -683,3 +683,26 @@ def test_vibronic_sop_is_the_model_formula():
         want = want + gq[0, s] * k3(P[s], I3, Q(4) @ Q(4))
     want = want + lam[0] * k3(sx, Q(3), I4)
     assert np.abs(got - want).max() <= 1e-14
+
+
+def test_spin_boson_sop_is_the_model_formula():
+    """The shared spin-boson generator against eps/2 sz + delta/2 sx
+    + sz sum_k g_k (a_k + a_k^+) + sum_k w_k n_k written with Kronecker
+    products (basis |0> = up)."""
+    t = W.build_tree(("node", 1, [("leaf", 2, 2, "s"), ("leaf", 3, 3, "b0"), ("leaf", 4, 4, "b1")]))
+    s, b0, b1 = (t.leaf_of_label(x) for x in ("s", "b0", "b1"))
+    g, w = [0.3, -0.2], [0.7, 1.9]
+    H = W.spin_boson_sop(s, [b0, b1], [3, 4], 0.4, 1.1, g, w)
+    got = exact.full_hamiltonian(t, H).toarray()
+
+    def ops(n):
+        a = np.diag(np.sqrt(np.arange(1, n)), 1)
+        return a + a.T, np.diag(np.arange(n, dtype=float))
+    (x3, n3), (x4, n4) = ops(3), ops(4)
+    sz, sx = np.diag([1.0, -1.0]), np.array([[0.0, 1.0], [1.0, 0.0]])
+    I2, I3, I4 = np.eye(2), np.eye(3), np.eye(4)
+    k3 = lambda A, B, C: np.kron(np.kron(A, B), C)
+    want = (0.2 * k3(sz, I3, I4) + 0.55 * k3(sx, I3, I4)
+            + g[0] * k3(sz, x3, I4) + g[1] * k3(sz, I3, x4)
+            + w[0] * k3(I2, n3, I4) + w[1] * k3(I2, I3, n4))
+    assert np.abs(got - want).max() <= 1e-14
