@@ -179,12 +179,16 @@ ttn_status upload_ops(ttn_ctx* c) {
     const OpsLayout L = ops_layout(P);
     const size_t off_table = L.off_table, off_entries = L.off_entries, off_ops = L.off_ops, off_inst = L.off_inst;
     const size_t total = L.total;
-    free_ops(c);
-    char* arena = nullptr;
-    cudaError_t ae = dev_alloc(c, &arena, total);
-    if (ae != cudaSuccess) return alloc_fail(c, ae, "device allocation (operators)");
-    c->d_ops = arena;
-    c->ops_bytes = total;
+    if (!(c->d_ops && c->ops_bytes == total)) {
+        // a layout of the same size (new coefficients, same structure) reuses the arena
+        free_ops(c);
+        char* arena = nullptr;
+        cudaError_t ae = dev_alloc(c, &arena, total);
+        if (ae != cudaSuccess) return alloc_fail(c, ae, "device allocation (operators)");
+        c->d_ops = arena;
+        c->ops_bytes = total;
+    }
+    c->rdm_p.clear(); c->vac_p.clear(); c->to_root_p.clear();
     std::vector<char> host(total, 0);
     // constant slots
     for (auto& s : P.slots)
