@@ -77,10 +77,14 @@ typedef struct {
                             the orthogonality centre on the bond's parent and
                             adds to the child the dominant eigenvectors of the
                             two-site energy-variance operator (1-P) G (1-P_S)
-                            that pass the criterion (at most 16 per bond and
-                            growth); after each growth the centre returns to
-                            the root and the pass restarts, until a pass adds
-                            nothing.  ttn_bond_dims reports the result.          */
+                            that pass the criterion (every one that passes, up
+                            to chi_max); after each growth the centre returns
+                            to the root and the pass restarts, until a pass
+                            adds nothing.  ttn_bond_dims reports the result.
+                            A bond whose terms have more than 32 distinct
+                            coupling channels, or a channel space (channels x
+                            bond dimension) above 512, cannot be tested:
+                            TTN_E_INVALID.                                       */
     double qr_rank_tol;  /* a QR column whose remainder has norm <= qr_rank_tol
                             * ||M||_F is treated as zero and completed by the
                             deterministic unit vector (unoccupied function);
@@ -294,7 +298,9 @@ ttn_status ttn_heff_apply(void* stream, int D, const int* dims, int n_terms, con
  * device current) and caches it; make that first call before any stream
  * capture.  All calls share the one array, and it keeps the contents of the
  * last call: calls whose work can overlap on the GPU (several streams or
- * host threads) race on it and must be serialised by the caller.  Runs one
+ * host threads) race on it -- on the term tables copied into it at the
+ * start of a call as well as on the three scratch tensors -- and must be
+ * serialised by the caller.  Runs one
  * thread block on `stream` and waits for it; errors through
  * ttn_last_error(NULL). */
 ttn_status ttn_heff_apply_noalloc(void* stream, int D, const int* dims, int n_terms, const ttn_c128* coeff,
@@ -305,6 +311,29 @@ ttn_status ttn_heff_apply_noalloc(void* stream, int D, const int* dims, int n_te
  * ttn_create calls allocate (the library carries its own CUDA runtime, so
  * a device selected through another runtime, e.g. PyTorch's, is not seen). */
 ttn_status ttn_set_device(int device);
+
+/* Thread blocks that one instance of ctx runs on (no counterpart in the
+ * paper: how a node update is spread over the GPU).  The sweep is a chain
+ * of dependent node updates (Sec. II.C), so a large instance is sped up by
+ * sharing each node's contractions, Krylov recurrences and QR among the
+ * blocks of a thread-block cluster (distributed shared memory for the
+ * team's sums, cluster barriers between phases).
+ *   blocks  0 = automatic (default): one block per 4096 elements of the
+ *           largest node tensor, a power of two, at most 16 -- a tree with
+ *           nodes of 98 304 elements (the 2 x 24 vibronic tree) gets 16,
+ *           one with nodes of a few hundred elements 1;
+ *           1 = one thread block of 256 threads;
+ *           2, 4, 8, 16 = a cluster of that many blocks of 512 threads.
+ * A context whose largest index dimension exceeds 45 always runs on at
+ * least 2 blocks.  ttn_step_batch runs every instance of a batch on the
+ * largest count any of its contexts set explicitly (automatic contexts
+ * count as 1 there: batches are spread over instances instead).  The
+ * result of a step depends on the block count only through rounding.
+ * Errors: TTN_E_INVALID for any other count. */
+ttn_status ttn_set_cluster(ttn_ctx* ctx, int blocks);
+
+/* The block count ttn_step uses for ctx with its current plan. */
+ttn_status ttn_get_cluster(const ttn_ctx* ctx, int* blocks);
 
 /* Step statistics of a context: total steps done since creation, the
  * algorithmic floating-point operations executed by its device programs

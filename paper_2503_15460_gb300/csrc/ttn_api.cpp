@@ -86,6 +86,15 @@ TtnInstance ttn::make_instance(ttn_ctx* c, const DevProgram& p) {
 
 ttn_status ttn::ctx_fail(ttn_ctx* c, ttn_status s, const std::string& msg) { return fail(c, s, msg); }
 
+int ttn::ctx_cluster(const ttn_ctx* c) {
+    const int need = c->plan.max_chi > kSoloMaxDim ? 2 : 1;
+    if (c->cluster_req > 0) return std::max(c->cluster_req, need);
+    int64_t per = c->plan.smax / 4096;
+    int k = 1;
+    while (k * 2 <= per && k < TTN_MAX_CLUSTER) k *= 2;
+    return std::max(k, need);
+}
+
 namespace {
 
 using ttn::make_instance;
@@ -146,7 +155,7 @@ ttn_status run_program(ttn_ctx* c, const DevProgram& p, double dt, int nrep) {
     if (p.n_ops == 0 || nrep == 0) return TTN_OK;
     TtnInstance in = make_instance(c, p);
     CK(cudaMemcpyAsync(c->d_inst, &in, sizeof(in), cudaMemcpyHostToDevice, c->stream), "instance upload");
-    int e = ttn_launch_program(c->precision, c->d_inst, 1, dt, nrep, c->stream);
+    int e = ttn_launch_program(c->precision, ttn::ctx_cluster(c), c->d_inst, 1, dt, nrep, c->stream);
     if (e != 0) return cuda_fail(c, (cudaError_t)e, "kernel launch");
     return check_status(c);
 }
@@ -158,6 +167,10 @@ ttn_status check_status_spawn(ttn_ctx* c, bool* hit) {
     *hit = st == TTN_STATUS_SPAWN_HIT;
     if (*hit) return TTN_OK;
     if (st == 4) return fail(c, TTN_E_NOCONV, "Krylov exponential did not converge");
+    if (st == TTN_STATUS_SPAWN_SPACE)
+        return fail(c, TTN_E_INVALID, "subspace expansion: a bond has more than " +
+                    std::to_string(TTN_SPAWN_MAX_CHANNELS) + " up channels or a channel space above " +
+                    std::to_string(TTN_SPAWN_MAX_K));
     if (st != 0) return fail(c, TTN_E_CUDA, "device reported status " + std::to_string(st));
     return TTN_OK;
 }
@@ -316,7 +329,7 @@ ttn_status expand_pass(ttn_ctx* c, double dt, double eps, int chi_max) {
         TtnInstance in = make_instance(c, c->spawn_p);
         in.chi_max = chi_max; in.spawn_eps = eps; in.spawn_dt = dt;
         CK(cudaMemcpyAsync(c->d_inst, &in, sizeof(in), cudaMemcpyHostToDevice, c->stream), "instance upload");
-        int e = ttn_launch_program(c->precision, c->d_inst, 1, dt, 1, c->stream);
+        int e = ttn_launch_program(c->precision, ttn::ctx_cluster(c), c->d_inst, 1, dt, 1, c->stream);
         if (e != 0) return cuda_fail(c, (cudaError_t)e, "kernel launch");
         bool hit = false;
         ttn_status s = check_status_spawn(c, &hit);
@@ -821,8 +834,16 @@ ttn_status ttn_step_batch(ttn_ctx* const* ctxs, int n, double dt, int nsteps, co
     }
     std::vector<TtnInstance> ins(n);
     for (int i = 0; i < n; ++i) ins[i] = make_instance(ctxs[i], ctxs[i]->step_p);
+    // one launch: every instance gets the largest team any of them asks
+    // for (automatic choice in a batch: one block each unless a dimension
+    // needs a cluster)
+    int cluster = 1;
+    for (int i = 0; i < n; ++i) {
+        const int need = ctxs[i]->plan.max_chi > ttn::kSoloMaxDim ? 2 : 1;
+        cluster = std::max(cluster, ctxs[i]->cluster_req > 0 ? std::max(ctxs[i]->cluster_req, need) : need);
+    }
     CK(cudaMemcpyAsync(c->d_batch, ins.data(), sizeof(TtnInstance) * n, cudaMemcpyHostToDevice, c->stream), "batch upload");
-    int e = ttn_launch_program(c->precision, c->d_batch, n, dt, nsteps, c->stream);
+    int e = ttn_launch_program(c->precision, cluster, c->d_batch, n, dt, nsteps, c->stream);
     if (e != 0) return cuda_fail(c, (cudaError_t)e, "kernel launch");
     CK(cudaStreamSynchronize(c->stream), "stream synchronize");
     for (int i = 0; i < n; ++i) {
@@ -1039,6 +1060,20 @@ ttn_status ttn_heff_apply_noalloc(void* stream, int D, const int* dims, int n_te
                                                          D, dims, x, y, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(c, e, "ttn_heff_apply_noalloc");
+    return TTN_OK;
+}
+
+ttn_status ttn_set_cluster(ttn_ctx* c, int blocks) {
+    if (!c) return fail(nullptr, TTN_E_INVALID, "ctx is NULL");
+    if (blocks < 0 || blocks > TTN_MAX_CLUSTER || (blocks & (blocks - 1)) != 0)
+        return fail(c, TTN_E_INVALID, "blocks must be 0 (automatic), 1, 2, 4, 8 or 16");
+    c->cluster_req = blocks;
+    return TTN_OK;
+}
+
+ttn_status ttn_get_cluster(const ttn_ctx* c, int* blocks) {
+    if (!c || !blocks) return fail(nullptr, TTN_E_INVALID, "NULL argument");
+    *blocks = ttn::ctx_cluster(c);
     return TTN_OK;
 }
 

@@ -62,12 +62,22 @@ struct ttn_ctx {
     int sop_herm = 1;
     int64_t steps_total = 0;
     int64_t spawned = 0;            // single-particle functions added by expansion
+    // Thread blocks per instance: 0 = chosen from the plan, 1 = one block,
+    // 2..16 = a thread-block cluster of that size.
+    int cluster_req = 0;
 };
 
 namespace ttn {
 
 // Device descriptor of one of the context's programs (resident contexts).
 TtnInstance make_instance(ttn_ctx* c, const DevProgram& p);
+// Largest tensor index dimension one thread block handles (the Gram
+// contraction keeps a 2 x 2 block of a dim x dim result per thread, twice).
+constexpr int kSoloMaxDim = 45;
+// Thread blocks one instance of c runs on: the caller's choice, else one
+// block per 4096 elements of the largest node tensor (a power of two, at
+// most 16); at least 2 when an index dimension exceeds kSoloMaxDim.
+int ctx_cluster(const ttn_ctx* c);
 // Record a failure on c (or, for c == NULL, for ttn_last_error(NULL)).
 ttn_status ctx_fail(ttn_ctx* c, ttn_status s, const std::string& msg);
 // Bytes ctx_materialize allocates for the current plan.

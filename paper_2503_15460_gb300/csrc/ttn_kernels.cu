@@ -1,1549 +1,81 @@
-// libttn device code: the sweep interpreter and its building blocks.
-//
-// One thread block executes the whole op list of one TTN instance (a node
-// update is a dependent chain of small contractions, so the work of one
-// instance stays on one SM and instances run side by side).  All
-// operations below are written for the whole block; __syncthreads()
-// separates dependent phases.
-//
-// T is the bulk element type: double2 (complex128 mode) or float2 (mixed
-// mode).  Scalars that steer the algorithm -- Krylov coefficients, norms,
-// the small projected exponential, Householder scalars -- are FP64 in both
-// modes, and the QR works on an FP64 copy of the matricised tensor.
+// libttn launch dispatch, the kernel-level effective-Hamiltonian entry
+// point and its allocation-free variant.  The sweep interpreter itself is in
+// ttn_device.cuh, compiled once per variant (ttn_var_*.cu).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <mutex>
-#ifdef TTN_SPAWN_DEBUG
-#include <cstdio>
-#endif
 
-#include "ttn_program.h"
+#include "ttn_device.cuh"
 #include "ttn_launch.h"
 
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
-
-// Algorithmic floating-point operations of this block (complex multiply-add
-// = 8), accumulated by thread 0 and flushed to the instance counter at exit.
-__shared__ double s_flops;
-// The part of them executed in FP64 arithmetic (element type complex128).
-__shared__ double s_flops64;
-template <class T>
-__device__ __forceinline__ void count_flops_t(double f) {
-    if (threadIdx.x == 0) {
-        s_flops += f;
-        if (sizeof(T) == 16) s_flops64 += f;
-    }
-}
-
-// Sub-phase cycle counters (thread 0), flushed with the op counters.
-__shared__ unsigned long long s_sub[8];
-__device__ __forceinline__ long long sub_start() { return clock64(); }
-__device__ __forceinline__ void sub_stop(int idx, long long t0) {
-    if (threadIdx.x == 0) s_sub[idx] += (unsigned long long)(clock64() - t0);
-}
-
-// Dynamic shared memory: a staging area for operator matrices and tiles.
-constexpr int kStageBytes = 64 * 1024;
-extern __shared__ __align__(16) unsigned char dyn_smem[];
-
-// ---------------------------------------------------------------------------
-// complex helpers
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ double2 cd(double2 a) { return a; }
-__device__ __forceinline__ double2 cd(float2 a) { return make_double2(a.x, a.y); }
-template <class T> __device__ __forceinline__ T cT(double2 a);
-template <> __device__ __forceinline__ double2 cT<double2>(double2 a) { return a; }
-template <> __device__ __forceinline__ float2 cT<float2>(double2 a) { return make_float2((float)a.x, (float)a.y); }
-
-__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ double2 cconjmul(double2 a, double2 b) {   // conj(a) * b
-    return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
-}
-__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
-__device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
-__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
-    double den = b.x * b.x + b.y * b.y;
-    return make_double2((a.x * b.x + a.y * b.y) / den, (a.y * b.x - a.x * b.y) / den);
-}
-
-// bulk multiply-accumulate in the element type's precision
-__device__ __forceinline__ void cfma(double2& acc, double2 a, double2 b) {
-    acc.x = fma(a.x, b.x, acc.x); acc.x = fma(-a.y, b.y, acc.x);
-    acc.y = fma(a.x, b.y, acc.y); acc.y = fma(a.y, b.x, acc.y);
-}
-__device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
-    acc.x = fmaf(a.x, b.x, acc.x); acc.x = fmaf(-a.y, b.y, acc.x);
-    acc.y = fmaf(a.x, b.y, acc.y); acc.y = fmaf(a.y, b.x, acc.y);
-}
-// acc += conj(a) * b in the element type's precision
-__device__ __forceinline__ void cfmaconj(double2& acc, double2 a, double2 b) {
-    acc.x = fma(a.x, b.x, acc.x); acc.x = fma(a.y, b.y, acc.x);
-    acc.y = fma(a.x, b.y, acc.y); acc.y = fma(-a.y, b.x, acc.y);
-}
-__device__ __forceinline__ void cfmaconj(float2& acc, float2 a, float2 b) {
-    acc.x = fmaf(a.x, b.x, acc.x); acc.x = fmaf(a.y, b.y, acc.x);
-    acc.y = fmaf(a.x, b.y, acc.y); acc.y = fmaf(-a.y, b.x, acc.y);
-}
-template <class T> __device__ __forceinline__ T czero();
-template <> __device__ __forceinline__ double2 czero<double2>() { return make_double2(0.0, 0.0); }
-template <> __device__ __forceinline__ float2 czero<float2>() { return make_float2(0.f, 0.f); }
-
-__device__ __forceinline__ double2 warp_sum(double2 v) {
-    for (int o = 16; o > 0; o >>= 1) {
-        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
-        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
-    }
-    return v;
-}
-__device__ __forceinline__ double warp_max(double v) {
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
-// ---------------------------------------------------------------------------
-// shared scratch
-// ---------------------------------------------------------------------------
-struct Smem {
-    double2 H[(TTN_KMAX + 1) * TTN_KMAX];   // projected matrix, row-major, ld TTN_KMAX
-    double2 y[TTN_KMAX + 1];
-    double2 u[TTN_KMAX + 1];
-    double2 dots[TTN_KMAX + 1];
-    double2 red[kWarps * 4];
-    double2 bc[4];
-    double2 qtau[TTN_MAXCHI];
-    int qskip[TTN_MAXCHI];
-    double qsign[TTN_MAXCHI];
-    int flag;
-};
-
-__device__ double2 block_sum(double2 v, Smem& sm) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    v = warp_sum(v);
-    if (lane == 0) sm.red[warp] = v;
-    __syncthreads();
-    if (warp == 0) {
-        double2 w = lane < kWarps ? sm.red[lane] : make_double2(0.0, 0.0);
-        w = warp_sum(w);
-        if (lane == 0) sm.bc[0] = w;
-    }
-    __syncthreads();
-    double2 r = sm.bc[0];
-    __syncthreads();
-    return r;
-}
-
-// Four block-wide sums at once (one barrier round); results in sm.bc[0..3].
-__device__ void block_sum4(double2 v[4], Smem& sm) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        v[q] = warp_sum(v[q]);
-        if (lane == 0) sm.red[warp * 4 + q] = v[q];
-    }
-    __syncthreads();
-    if (warp == 0) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            double2 w = lane < kWarps ? sm.red[lane * 4 + q] : make_double2(0.0, 0.0);
-            w = warp_sum(w);
-            if (lane == 0) sm.bc[q] = w;
-        }
-    }
-    __syncthreads();
-}
-
-template <class T>
-__device__ double2 block_dot(const T* __restrict__ a, const T* __restrict__ b, int64_t n, Smem& sm) {
-    T acc = czero<T>();
-    for (int64_t i = threadIdx.x; i < n; i += kThreads) cfmaconj(acc, a[i], b[i]);
-    count_flops_t<T>(8.0 * n);
-    return block_sum(cd(acc), sm);
-}
-
-// ---------------------------------------------------------------------------
-// tensor primitives
-// ---------------------------------------------------------------------------
-struct Shape {
-    int D;
-    int d[TTN_MAXD];
-    __device__ int64_t size() const { int64_t s = 1; for (int j = 0; j < D; ++j) s *= d[j]; return s; }
-    __device__ int64_t before(int k) const { int64_t s = 1; for (int j = 0; j < k; ++j) s *= d[j]; return s; }
-    __device__ int64_t after(int k) const { int64_t s = 1; for (int j = k + 1; j < D; ++j) s *= d[j]; return s; }
-};
-
-// out[l, p, r] (+)= w * sum_m M[p, m] in[l, m, r]   (M: nout x nin, or its
-// transpose stored nin x nout when transM).  Generic version: one output
-// per thread.
-template <class T>
-__device__ void mode_prod_simple(T* __restrict__ out, const T* __restrict__ in, int64_t L, int nin, int nout,
-                                 int64_t R, const T* __restrict__ M, bool transM, double2 w, bool accumulate) {
-    const int64_t total = L * nout * R;
-    const T wt = cT<T>(w);
-    for (int64_t idx = threadIdx.x; idx < total; idx += kThreads) {
-        const int64_t r = idx % R;
-        const int64_t t = idx / R;
-        const int p = (int)(t % nout);
-        const int64_t l = t / nout;
-        const T* src = in + l * nin * R + r;
-        T acc = czero<T>();
-        if (transM) {
-            for (int m = 0; m < nin; ++m) cfma(acc, M[m * nout + p], src[m * R]);
-        } else {
-            const T* row = M + p * nin;
-            for (int m = 0; m < nin; ++m) cfma(acc, row[m], src[m * R]);
-        }
-        T v = czero<T>();
-        cfma(v, wt, acc);
-        if (accumulate) { T o = out[idx]; o.x += v.x; o.y += v.y; out[idx] = o; }
-        else out[idx] = v;
-    }
-}
-
-// Square mode product with the matrix staged in shared memory and each
-// fibre in[l, :, r] held in registers: every thread produces all n outputs
-// of its fibre, reading the matrix rows as shared-memory broadcasts.  Two
-// outputs are accumulated per pass, so four independent FMA chains hide
-// the FMA latency (one pass per output left half of the issue slots idle).
-template <class T, int MAXN>
-__device__ void mode_prod_tiled(T* __restrict__ out, const T* __restrict__ in, int64_t L, int n, int64_t R,
-                                const T* __restrict__ M, double2 w, bool accumulate) {
-    T* Ms = (T*)dyn_smem;
-    for (int i = threadIdx.x; i < n * n; i += kThreads) Ms[i] = M[i];
-    __syncthreads();
-    const int64_t F = L * R;
-    const T wt = cT<T>(w);
-    for (int64_t f = threadIdx.x; f < F; f += kThreads) {
-        const int64_t l = f / R, r = f - (f / R) * R;
-        const T* src = in + l * n * R + r;
-        T* dst = out + l * n * R + r;
-        T x[MAXN];
-#pragma unroll
-        for (int m = 0; m < MAXN; ++m) x[m] = (m < n) ? src[m * R] : czero<T>();
-        int p = 0;
-        for (; p + 1 < n; p += 2) {
-            const T* row0 = Ms + p * n;
-            const T* row1 = row0 + n;
-            T a0 = czero<T>(), a1 = czero<T>();
-#pragma unroll
-            for (int m = 0; m < MAXN; ++m)
-                if (m < n) { cfma(a0, row0[m], x[m]); cfma(a1, row1[m], x[m]); }
-            T v0 = czero<T>(), v1 = czero<T>();
-            cfma(v0, wt, a0);
-            cfma(v1, wt, a1);
-            if (accumulate) {
-                T o0 = dst[p * R], o1 = dst[(p + 1) * R];
-                o0.x += v0.x; o0.y += v0.y; o1.x += v1.x; o1.y += v1.y;
-                dst[p * R] = o0; dst[(p + 1) * R] = o1;
-            } else {
-                dst[p * R] = v0; dst[(p + 1) * R] = v1;
-            }
-        }
-        if (p < n) {
-            const T* row = Ms + p * n;
-            T acc = czero<T>();
-#pragma unroll
-            for (int m = 0; m < MAXN; ++m)
-                if (m < n) cfma(acc, row[m], x[m]);
-            T v = czero<T>();
-            cfma(v, wt, acc);
-            if (accumulate) { T o = dst[p * R]; o.x += v.x; o.y += v.y; dst[p * R] = o; }
-            else dst[p * R] = v;
-        }
-    }
-    __syncthreads();
-}
-
-template <class T>
-__device__ void mode_prod(T* __restrict__ out, const T* __restrict__ in, int64_t L, int nin, int nout,
-                          int64_t R, const T* __restrict__ M, bool transM, double2 w, bool accumulate) {
-    count_flops_t<T>(8.0 * (double)(L * nout * R) * nin);
-    if (transM || nin != nout || nin > (sizeof(T) == 16 ? 16 : 32)) {
-        mode_prod_simple(out, in, L, nin, nout, R, M, transM, w, accumulate);
-        return;
-    }
-    if (nin <= 2) mode_prod_tiled<T, 2>(out, in, L, nin, R, M, w, accumulate);
-    else if (nin <= 4) mode_prod_tiled<T, 4>(out, in, L, nin, R, M, w, accumulate);
-    else if (nin <= 8) mode_prod_tiled<T, 8>(out, in, L, nin, R, M, w, accumulate);
-    else if (nin <= 12) mode_prod_tiled<T, 12>(out, in, L, nin, R, M, w, accumulate);
-    else if (nin <= 16) mode_prod_tiled<T, 16>(out, in, L, nin, R, M, w, accumulate);
-    else if (sizeof(T) == 8 && nin <= 24) mode_prod_tiled<T, (sizeof(T) == 8 ? 24 : 16)>(out, in, L, nin, R, M, w, accumulate);
-    else if (sizeof(T) == 8) mode_prod_tiled<T, (sizeof(T) == 8 ? 32 : 16)>(out, in, L, nin, R, M, w, accumulate);
-}
-
-template <class T>
-__device__ void copy_vec(T* __restrict__ dst, const T* __restrict__ src, int64_t n) {
-    for (int64_t i = threadIdx.x; i < n; i += kThreads) dst[i] = src[i];
-}
-
-// Chain of mode products of one entry over the modes != skip (skip = -1:
-// all modes).  Returns the buffer holding the result (src itself if the
-// entry has no factor there).  The last factor is written to `last_out`
-// with weight w (accumulate) when last_out != nullptr.
-template <class T>
-__device__ const T* apply_chain(const T* src, T* t1, T* t2, const Shape& sh, const TtnEntry& e,
-                                const TtnSlot* slots, int skip, T* last_out, double2 w) {
-    int modes[TTN_MAXD], nf = 0;
-    for (int j = 0; j < sh.D; ++j)
-        if (j != skip && e.slot[j] >= 0) modes[nf++] = j;
-    const T* cur = src;
-    for (int f = 0; f < nf; ++f) {
-        const int j = modes[f];
-        const TtnSlot s = slots[e.slot[j]];
-        const T* M = (const T*)s.ptr;
-        const int64_t L = sh.before(j), R = sh.after(j);
-        const int n = sh.d[j];
-        if (f == nf - 1 && last_out) {
-            mode_prod(last_out, cur, L, n, n, R, M, false, w, true);
-            __syncthreads();
-            return last_out;
-        }
-        T* dst = (cur == t1) ? t2 : t1;
-        mode_prod(dst, cur, L, n, n, R, M, false, make_double2(1.0, 0.0), false);
-        __syncthreads();
-        cur = dst;
-    }
-    return cur;
-}
-
-__device__ __forceinline__ int last_factor(const TtnEntry& e, int D) {
-    int lm = -1;
-    for (int j = 0; j < D; ++j) if (e.slot[j] >= 0) lm = j;
-    return lm;
-}
-__device__ __forceinline__ int n_factors(const TtnEntry& e, int D) {
-    int n = 0;
-    for (int j = 0; j < D; ++j) n += e.slot[j] >= 0;
-    return n;
-}
-
-// out = sum_e w_e (x_j M_ej) in   (effective Hamiltonian / bond operator).
-// Entries are ordered so that those sharing their last factor (highest mode
-// with a matrix, same slot) are adjacent; their partial chains are summed in
-// t3 and the shared factor is applied once.
-template <class T>
-__device__ void heff_apply(T* __restrict__ out, const T* __restrict__ in, T* t1, T* t2, T* t3, const Shape& sh,
-                           const TtnEntry* es, int ne, const TtnSlot* slots) {
-    const int64_t S = sh.size();
-    for (int64_t i = threadIdx.x; i < S; i += kThreads) out[i] = czero<T>();
-    __syncthreads();
-    int i = 0;
-    while (i < ne) {
-        const TtnEntry e = es[i];
-        const double2 w = make_double2(e.wr, e.wi);
-        const int lm = last_factor(e, sh.D);
-        if (lm < 0) {
-            const T wt = cT<T>(w);
-            for (int64_t q = threadIdx.x; q < S; q += kThreads) {
-                T o = out[q]; cfma(o, wt, in[q]); out[q] = o;
-            }
-            __syncthreads();
-            ++i;
-            continue;
-        }
-        int j = i + 1;
-        if (n_factors(e, sh.D) >= 2)
-            while (j < ne && last_factor(es[j], sh.D) == lm && es[j].slot[lm] == e.slot[lm] &&
-                   n_factors(es[j], sh.D) >= 2) ++j;
-        if (j - i == 1) {
-            apply_chain(in, t1, t2, sh, e, slots, -1, out, w);
-            i = j;
-            continue;
-        }
-        for (int64_t q = threadIdx.x; q < S; q += kThreads) t3[q] = czero<T>();
-        __syncthreads();
-        for (int q = i; q < j; ++q) {
-            const TtnEntry eq = es[q];
-            apply_chain(in, t1, t2, sh, eq, slots, lm, t3, make_double2(eq.wr, eq.wi));
-        }
-        const int n = sh.d[lm];
-        mode_prod(out, (const T*)t3, sh.before(lm), n, n, sh.after(lm), (const T*)slots[e.slot[lm]].ptr, false,
-                  make_double2(1.0, 0.0), true);
-        __syncthreads();
-        i = j;
-    }
-}
-
-// G[a, b] += w * sum_{other indices} conj(X[.., a, ..]) Y[.., b, ..]   (index k kept)
-// Tiles of X and Y (all chi values of the kept index for OT positions of
-// the others) are staged in shared memory; every thread accumulates a 2x2
-// block of G, small G are split over groups of positions, and the group
-// partials are reduced in a fixed order (deterministic).
-template <class T>
-__device__ void gram_acc(T* G, const T* __restrict__ X, const T* __restrict__ Y, const Shape& sh, int k, double2 w) {
-    const int chi = sh.d[k];
-    const int64_t L = sh.before(k), R = sh.after(k), O = L * R;
-    count_flops_t<T>(8.0 * (double)O * chi * chi);
-    int OT = (kStageBytes / 2) / (chi * (int)sizeof(T));
-    if (OT > 128) OT = 128;
-    T* Xs = (T*)dyn_smem;            // [OT][chi]
-    T* Ys = Xs + OT * chi;
-    const int tn = (chi + 1) / 2, ntile = tn * tn;
-    int groups = kThreads / ntile;
-    if (groups < 1) groups = 1;
-    if (groups > 8) groups = 8;
-    const int tid = threadIdx.x;
-    const bool active = tid < ntile * groups || ntile > kThreads;
-    T acc[2][2][2];
-    const int nrep = (ntile + kThreads - 1) / kThreads;      // tiles per thread when chi > 32
-#pragma unroll
-    for (int q = 0; q < 2; ++q)
-#pragma unroll
-        for (int i = 0; i < 2; ++i)
-#pragma unroll
-            for (int j = 0; j < 2; ++j) acc[q][i][j] = czero<T>();
-    const int g = (ntile >= kThreads) ? 0 : tid / ntile;
-    const int gcount = (ntile >= kThreads) ? 1 : groups;
-    for (int64_t o0 = 0; o0 < O; o0 += OT) {
-        const int nt = (int)((O - o0) < OT ? (O - o0) : OT);
-        if (R == 1) {
-            const T* xs = X + o0 * chi;
-            const T* ys = Y + o0 * chi;
-            for (int i = tid; i < nt * chi; i += kThreads) { Xs[i] = xs[i]; Ys[i] = ys[i]; }
-        } else {
-            for (int i = tid; i < nt * chi; i += kThreads) {
-                const int oo = i % nt, a = i / nt;
-                const int64_t o = o0 + oo, l = o / R, r = o - (o / R) * R;
-                const int64_t src = (l * chi + a) * R + r;
-                Xs[oo * chi + a] = X[src];
-                Ys[oo * chi + a] = Y[src];
-            }
-        }
-        __syncthreads();
-        if (active) {
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                if (q >= nrep) break;
-                const int tile = (ntile >= kThreads) ? tid + q * kThreads : tid % ntile;
-                if (tile >= ntile) break;
-                const int a0 = 2 * (tile / tn), b0 = 2 * (tile % tn);
-                const bool a1ok = a0 + 1 < chi, b1ok = b0 + 1 < chi;
-                for (int oo = g; oo < nt; oo += gcount) {
-                    const T x0 = Xs[oo * chi + a0];
-                    const T x1 = a1ok ? Xs[oo * chi + a0 + 1] : czero<T>();
-                    const T y0 = Ys[oo * chi + b0];
-                    const T y1 = b1ok ? Ys[oo * chi + b0 + 1] : czero<T>();
-                    cfmaconj(acc[q][0][0], x0, y0); cfmaconj(acc[q][0][1], x0, y1);
-                    cfmaconj(acc[q][1][0], x1, y0); cfmaconj(acc[q][1][1], x1, y1);
-                }
-            }
-        }
-        __syncthreads();
-    }
-    // write partials P[g][a][b] and reduce over g in order
-    T* Pp = (T*)dyn_smem;
-    if (active) {
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            if (q >= nrep) break;
-            const int tile = (ntile >= kThreads) ? tid + q * kThreads : tid % ntile;
-            if (tile >= ntile) break;
-            const int a0 = 2 * (tile / tn), b0 = 2 * (tile % tn);
-            for (int i = 0; i < 2; ++i)
-                for (int j = 0; j < 2; ++j)
-                    if (a0 + i < chi && b0 + j < chi) Pp[((int64_t)g * chi + a0 + i) * chi + b0 + j] = acc[q][i][j];
-        }
-    }
-    __syncthreads();
-    for (int ab = tid; ab < chi * chi; ab += kThreads) {
-        double2 sum = make_double2(0.0, 0.0);
-        for (int gg = 0; gg < gcount; ++gg) sum = cadd(sum, cd(Pp[(int64_t)gg * chi * chi + ab]));
-        G[ab] = cT<T>(cadd(cd(G[ab]), cmul(w, sum)));
-    }
-    __syncthreads();
-}
-
-// Environment build: for every output slot, out = Q^dag (sum_e w_e x_{j != keep} M_ej) Q.
-// The chains of all entries of one output are summed in ysum first, so each
-// output costs one Gram contraction.
-template <class T>
-__device__ void env_build(const T* Q, T* t1, T* t2, T* ysum, const Shape& sh, int keep, const TtnEntry* es, int ne,
-                          const TtnSlot* slots) {
-    const int64_t S = sh.size();
-    int i = 0;
-    while (i < ne) {
-        const int outs = es[i].out;
-        int j = i;
-        while (j < ne && es[j].out == outs) ++j;
-        T* out = (T*)slots[outs].ptr;
-        const int n = slots[outs].rows * slots[outs].cols;
-        for (int q = threadIdx.x; q < n; q += kThreads) out[q] = czero<T>();
-        const T* Y;
-        if (j - i == 1) {
-            const TtnEntry e = es[i];
-            Y = apply_chain(Q, t1, t2, sh, e, slots, keep, (T*)nullptr, make_double2(1.0, 0.0));
-            __syncthreads();
-            const long long tg = sub_start();
-            gram_acc(out, Q, Y, sh, keep, make_double2(e.wr, e.wi));
-            sub_stop(3, tg);
-        } else {
-            for (int64_t q = threadIdx.x; q < S; q += kThreads) ysum[q] = czero<T>();
-            __syncthreads();
-            for (int q = i; q < j; ++q) {
-                const TtnEntry e = es[q];
-                const double2 w = make_double2(e.wr, e.wi);
-                bool any = false;
-                for (int m = 0; m < sh.D; ++m) any |= (m != keep && e.slot[m] >= 0);
-                if (!any) {
-                    const T wt = cT<T>(w);
-                    for (int64_t x = threadIdx.x; x < S; x += kThreads) { T o = ysum[x]; cfma(o, wt, Q[x]); ysum[x] = o; }
-                    __syncthreads();
-                } else {
-                    apply_chain(Q, t1, t2, sh, e, slots, keep, ysum, w);
-                }
-            }
-            const long long tg = sub_start();
-            gram_acc(out, Q, (const T*)ysum, sh, keep, make_double2(1.0, 0.0));
-            sub_stop(3, tg);
-        }
-        __syncthreads();
-        i = j;
-    }
-}
-
-// out = sum w * M  (slot[0] = -1: w * identity)
-template <class T>
-__device__ void combo(const TtnEntry* es, int ne, const TtnSlot* slots) {
-    int prev = -1;
-    for (int ei = 0; ei < ne; ++ei) {
-        const TtnEntry e = es[ei];
-        T* out = (T*)slots[e.out].ptr;
-        const int n = slots[e.out].rows;
-        if (e.out != prev) {
-            for (int i = threadIdx.x; i < n * n; i += kThreads) out[i] = czero<T>();
-            __syncthreads();
-            prev = e.out;
-        }
-        const double2 w = make_double2(e.wr, e.wi);
-        const T* M = e.slot[0] >= 0 ? (const T*)slots[e.slot[0]].ptr : nullptr;
-        for (int i = threadIdx.x; i < n * n; i += kThreads) {
-            double2 m = M ? cd(M[i]) : make_double2((i / n == i % n) ? 1.0 : 0.0, 0.0);
-            out[i] = cT<T>(cadd(cd(out[i]), cmul(w, m)));
-        }
-        __syncthreads();
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Householder QR of the matricisation with index k as the column index.
-// A is overwritten by Q; R (n x n, FP64) is left in Wc's upper triangle with
-// signs in sm.qsign.  Rank-deficient columns (remainder norm <= tol ||A||_F)
-// get the identity reflector, as in the oracle's definition.
-// ---------------------------------------------------------------------------
-template <class T>
-__device__ void qr_mode(T* A, const Shape& sh, int k, double2* Wc, double2* Qc, double tol, Smem& sm) {
-    const int n = sh.d[k];
-    const int64_t L = sh.before(k), R = sh.after(k), m = L * R, S = m * n;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // gather column-major: Wc[j*m + (l*R + r)] = A[(l*n + j)*R + r]
-    double2 part = make_double2(0.0, 0.0);
-    for (int64_t idx = threadIdx.x; idx < S; idx += kThreads) {
-        const int64_t j = idx / m, I = idx % m;
-        const int64_t l = I / R, r = I % R;
-        double2 v = cd(A[(l * n + j) * R + r]);
-        Wc[idx] = v;
-        part.x += cabs2(v);
-    }
-    const double thr = tol * sqrt(block_sum(part, sm).x);
-    for (int j = 0; j < n; ++j) {
-        double2* x = Wc + (int64_t)j * m;
-        double2 s = make_double2(0.0, 0.0);
-        for (int64_t i = j + threadIdx.x; i < m; i += kThreads) s.x += cabs2(x[i]);
-        const double nrm = sqrt(block_sum(s, sm).x);
-        const double2 alpha = x[j];
-        if (nrm <= thr) {
-            for (int64_t i = j + 1 + threadIdx.x; i < m; i += kThreads) x[i] = make_double2(0.0, 0.0);
-            if (threadIdx.x == 0) { sm.qskip[j] = 1; sm.qtau[j] = make_double2(0.0, 0.0); }
-            __syncthreads();
-            continue;
-        }
-        const double beta = alpha.x >= 0.0 ? -nrm : nrm;
-        const double2 tau = cscale(csub(make_double2(beta, 0.0), alpha), 1.0 / beta);
-        const double2 scl = cdiv(make_double2(1.0, 0.0), csub(alpha, make_double2(beta, 0.0)));
-        for (int64_t i = j + 1 + threadIdx.x; i < m; i += kThreads) x[i] = cmul(x[i], scl);
-        __syncthreads();
-        if (threadIdx.x == 0) { x[j] = make_double2(beta, 0.0); sm.qskip[j] = 0; sm.qtau[j] = tau; }
-        const double2 ctau = make_double2(tau.x, -tau.y);
-        count_flops_t<double2>(16.0 * (double)(m - j) * (n - j - 1) + 8.0 * (m - j));
-        for (int c = j + 1 + warp; c < n; c += kWarps) {
-            double2* y = Wc + (int64_t)c * m;
-            double2 acc = make_double2(0.0, 0.0);
-            for (int64_t i = j + lane; i < m; i += 32) {
-                double2 v = (i == j) ? make_double2(1.0, 0.0) : x[i];
-                cfmaconj(acc, v, y[i]);
-            }
-            acc = warp_sum(acc);
-            const double2 f = cmul(ctau, acc);
-            const double2 nf = make_double2(-f.x, -f.y);
-            for (int64_t i = j + lane; i < m; i += 32) {
-                double2 v = (i == j) ? make_double2(1.0, 0.0) : x[i];
-                double2 yi = y[i];
-                cfma(yi, v, nf);
-                y[i] = yi;
-            }
-        }
-        __syncthreads();
-    }
-    // Q = H_0 .. H_{n-1} I[:, :n]
-    for (int64_t idx = threadIdx.x; idx < S; idx += kThreads) {
-        const int64_t c = idx / m, i = idx % m;
-        Qc[idx] = make_double2(i == c ? 1.0 : 0.0, 0.0);
-    }
-    __syncthreads();
-    for (int j = n - 1; j >= 0; --j) {
-        if (sm.qskip[j]) continue;
-        const double2 tau = sm.qtau[j];
-        const double2* x = Wc + (int64_t)j * m;
-        count_flops_t<double2>(16.0 * (double)(m - j) * (n - j));
-        for (int c = j + warp; c < n; c += kWarps) {
-            double2* y = Qc + (int64_t)c * m;
-            double2 acc = make_double2(0.0, 0.0);
-            for (int64_t i = j + lane; i < m; i += 32) {
-                double2 v = (i == j) ? make_double2(1.0, 0.0) : x[i];
-                cfmaconj(acc, v, y[i]);
-            }
-            acc = warp_sum(acc);
-            const double2 f = cmul(tau, acc);
-            const double2 nf = make_double2(-f.x, -f.y);
-            for (int64_t i = j + lane; i < m; i += 32) {
-                double2 v = (i == j) ? make_double2(1.0, 0.0) : x[i];
-                double2 yi = y[i];
-                cfma(yi, v, nf);
-                y[i] = yi;
-            }
-        }
-        __syncthreads();
-    }
-    // signs: diag(R) real >= 0
-    for (int j = threadIdx.x; j < n; j += kThreads)
-        sm.qsign[j] = (!sm.qskip[j] && Wc[(int64_t)j * m + j].x < 0.0) ? -1.0 : 1.0;
-    __syncthreads();
-    for (int64_t idx = threadIdx.x; idx < S; idx += kThreads) {
-        const int64_t j = idx / m, I = idx % m;
-        const int64_t l = I / R, r = I % R;
-        A[(l * n + j) * R + r] = cT<T>(cscale(Qc[idx], sm.qsign[j]));
-    }
-    __syncthreads();
-}
-
-// R[a][b] of the last QR (a <= b), sign-fixed
-__device__ __forceinline__ double2 qr_R(const double2* Wc, int64_t m, int a, int b, const Smem& sm) {
-    if (a > b) return make_double2(0.0, 0.0);
-    return cscale(Wc[(int64_t)b * m + a], sm.qsign[a]);
-}
-
-// ---------------------------------------------------------------------------
-// Small projected exponential: sm.y = exp(-i tau H_m) e_0 (warp 0).
-// Scaling into substeps of 1-norm <= 1, each summed as a Taylor series on
-// the vector (Moler & Van Loan, "Nineteen dubious ways", method 1 with
-// scaling); for a tridiagonal H only the band is used.
-// ---------------------------------------------------------------------------
-__device__ void small_expm(Smem& sm, int m, double tau, bool band) {
-    if ((threadIdx.x >> 5) != 0) return;
-    const int i = threadIdx.x & 31;
-    double colsum = 0.0;
-    if (i < m)
-        for (int r = 0; r < m; ++r) colsum += sqrt(cabs2(sm.H[r * TTN_KMAX + i]));
-    const double nrm = warp_max(colsum) * fabs(tau);
-    if (!(nrm <= 1e5)) {            // not finite or absurdly stiff: report NaN, caller fails
-        if (i < m) sm.y[i] = make_double2(NAN, NAN);
-        __syncwarp();
-        return;
-    }
-    // substeps of 1-norm <= 1; 18 Taylor terms leave a truncation below 1/19! ~ 8e-18
-    int s = (int)ceil(nrm);
-    if (s < 1) s = 1;
-    const double h = tau / s;
-    double2 y = make_double2(i == 0 ? 1.0 : 0.0, 0.0);
-    const int jlo = max(0, i - 1);
-    const int jhi = band ? min(m - 1, i + 1) : m - 1;
-    for (int step = 0; step < s; ++step) {
-        double2 term = y, acc = y;
-#pragma unroll 1
-        for (int kk = 1; kk <= 18; ++kk) {
-            sm.u[i] = term;
-            __syncwarp();
-            double2 nt = make_double2(0.0, 0.0);
-            if (i < m)
-                for (int j = jlo; j <= jhi; ++j) nt = cadd(nt, cmul(sm.H[i * TTN_KMAX + j], sm.u[j]));
-            __syncwarp();
-            const double f = h / kk;
-            term = (i < m) ? make_double2(nt.y * f, -nt.x * f) : make_double2(0.0, 0.0);
-            acc = cadd(acc, term);
-        }
-        y = acc;
-    }
-    if (i < m) sm.y[i] = y;
-    __syncwarp();
-}
-
-// ---------------------------------------------------------------------------
-// Krylov exponential x <- exp(-i tau Hop) x (Lanczos when herm, Arnoldi
-// otherwise; two classical Gram-Schmidt passes against the whole basis).
-// The basis V is kept in the bulk type TB; x (node tensor or bond matrix) in
-// the state type TS.  The result is assembled as
-//     x_new = y_0 x + ||x|| sum_{i>=1} y_i V_i
-// so that the leading term keeps the state's precision.
-// Stops on Saad's estimate h_{m+1,m} |e_m^T exp(-i tau H_m) e_1| <= tol.
-// Returns 1 when converged (x updated), 0 when kmax was reached, -1 on a
-// non-finite norm.
-// ---------------------------------------------------------------------------
-__device__ void jacobi_eigh(double2* A, double2* Vm, int n, Smem& sm);
-
-// Lowest Ritz pair of the m x m Hermitian tridiagonal Lanczos matrix in
-// sm.H (all threads): eigen-decomposition by cyclic Jacobi in the stage
-// buffer, eigenvector to sm.y[0..m), eigenvalue to sm.u[0].x.
-__device__ void lowest_ritz(Smem& sm, int m) {
-    double2* T = (double2*)(dyn_smem + 16384);
-    double2* Vm = (double2*)(dyn_smem + 32768);
-    for (int i = threadIdx.x; i < m * m; i += kThreads) {
-        const int r = i / m, c = i - (i / m) * m;
-        T[i] = sm.H[r * TTN_KMAX + c];
-    }
-    __syncthreads();
-    jacobi_eigh(T, Vm, m, sm);
-    if (threadIdx.x == 0) {
-        int imin = 0;
-        for (int i = 1; i < m; ++i)
-            if (T[i * m + i].x < T[imin * m + imin].x) imin = i;
-        for (int i = 0; i < m; ++i) sm.y[i] = Vm[i * m + imin];
-        sm.u[0] = make_double2(T[imin * m + imin].x, 0.0);
-    }
-    __syncthreads();
-}
-
-template <class TS, class TB>
-__device__ int krylov_once(TS* x, const Shape& sh, const TtnEntry* es, int ne, const TtnSlot* slots,
-                           double tau, int herm, double tol, int kmax, TB* V, int64_t smax, TB* t1, TB* t2,
-                           TB* t3, Smem& sm, int ground = 0) {
-    double logbound = 0.0;          // log(|tau|^m prod h_{i+1,i} / m!)
-    const int64_t S = sh.size();
-    double2 nb = make_double2(0.0, 0.0);
-    for (int64_t i = threadIdx.x; i < S; i += kThreads) nb.x += cabs2(cd(x[i]));
-    const double beta0 = sqrt(block_sum(nb, sm).x);
-    if (beta0 == 0.0) return 1;
-    if (!isfinite(beta0)) return -1;
-    for (int i = threadIdx.x; i < (TTN_KMAX + 1) * TTN_KMAX; i += kThreads) sm.H[i] = make_double2(0.0, 0.0);
-    {
-        const double inv = 1.0 / beta0;
-        for (int64_t i = threadIdx.x; i < S; i += kThreads) V[i] = cT<TB>(cscale(cd(x[i]), inv));
-    }
-    __syncthreads();
-    for (int j = 0; j < kmax; ++j) {
-        TB* vj = V + (int64_t)j * smax;
-        TB* w = V + (int64_t)(j + 1) * smax;
-        const long long th = sub_start();
-        heff_apply(w, vj, t1, t2, t3, sh, es, ne, slots);
-        sub_stop(0, th);
-        const long long tgs = sub_start();
-        for (int pass = 0; pass < 2; ++pass) {
-            for (int i0 = 0; i0 <= j; i0 += 4) {
-                const int nb = (j + 1 - i0) < 4 ? (j + 1 - i0) : 4;
-                TB acc[4] = {czero<TB>(), czero<TB>(), czero<TB>(), czero<TB>()};
-                for (int64_t e = threadIdx.x; e < S; e += kThreads) {
-                    const TB we = w[e];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        if (q < nb) cfmaconj(acc[q], V[(int64_t)(i0 + q) * smax + e], we);
-                }
-                double2 d[4] = {cd(acc[0]), cd(acc[1]), cd(acc[2]), cd(acc[3])};
-                block_sum4(d, sm);
-                if (threadIdx.x == 0)
-                    for (int q = 0; q < nb; ++q) {
-                        sm.dots[i0 + q] = sm.bc[q];
-                        sm.H[(i0 + q) * TTN_KMAX + j] = cadd(sm.H[(i0 + q) * TTN_KMAX + j], sm.bc[q]);
-                    }
-                __syncthreads();
-            }
-            count_flops_t<TB>(16.0 * (double)S * (j + 1));
-            int64_t e = threadIdx.x;
-            for (; e + kThreads < S; e += 2 * kThreads) {
-                TB a0 = w[e], a1 = w[e + kThreads];
-                for (int i = 0; i <= j; ++i) {
-                    const double2 h = sm.dots[i];
-                    const TB nh = cT<TB>(make_double2(-h.x, -h.y));
-                    const TB* Vi = V + (int64_t)i * smax + e;
-                    cfma(a0, nh, Vi[0]);
-                    cfma(a1, nh, Vi[kThreads]);
-                }
-                w[e] = a0;
-                w[e + kThreads] = a1;
-            }
-            if (e < S) {
-                TB acc = w[e];
-                for (int i = 0; i <= j; ++i) {
-                    const double2 h = sm.dots[i];
-                    cfma(acc, cT<TB>(make_double2(-h.x, -h.y)), V[(int64_t)i * smax + e]);
-                }
-                w[e] = acc;
-            }
-            __syncthreads();
-        }
-        if (herm && threadIdx.x == 0) {
-            sm.H[j * TTN_KMAX + j].y = 0.0;
-            for (int i = 0; i + 1 < j; ++i) sm.H[i * TTN_KMAX + j] = make_double2(0.0, 0.0);
-            if (j > 0) sm.H[(j - 1) * TTN_KMAX + j] = sm.H[j * TTN_KMAX + (j - 1)];
-        }
-        TB nwt = czero<TB>();
-        for (int64_t e = threadIdx.x; e < S; e += kThreads) cfmaconj(nwt, w[e], w[e]);
-        const double hnext = sqrt(block_sum(cd(nwt), sm).x);
-        if (threadIdx.x == 0) sm.H[(j + 1) * TTN_KMAX + j] = make_double2(hnext, 0.0);
-        __syncthreads();
-        sub_stop(1, tgs);
-        const int mm = j + 1;
-        if (!isfinite(hnext)) return -1;
-        // For a Hermitian tridiagonal H_m, |e_m^T exp(-i tau H_m) e_1| <= |tau|^(m-1)
-        // prod_{i<m-1} h_{i+1,i} / (m-1)!, so h_{m+1,m} times that bounds Saad's
-        // estimate; the small exponential is evaluated only once this bound is
-        // within 1e4 of the tolerance (always at kmax and on breakdown).
-        logbound += log(fmax(hnext, 1e-300)) + log(fabs(tau) + 1e-300) - log((double)mm);
-        const bool near = ground ? ((j & 1) == 1 || j == kmax - 1 || hnext == 0.0)
-                                 : (logbound <= log(1e4 * tol) || j == kmax - 1 || hnext == 0.0 || (j & 3) == 3);
-        if (!near) {
-            const double inv = 1.0 / hnext;
-            for (int64_t e = threadIdx.x; e < S; e += kThreads) w[e] = cT<TB>(cscale(cd(w[e]), inv));
-            __syncthreads();
-            continue;
-        }
-        if (ground) {
-            // lowest Ritz pair; Lanczos residual |h_{m+1,m} y_m| against tol * max(1, |theta|)
-            lowest_ritz(sm, mm);
-            const double theta = sm.u[0].x;
-            const double res = hnext * sqrt(cabs2(sm.y[j]));
-            if (!isfinite(res) || !isfinite(theta)) return -1;
-            const bool conv = res <= tol * fmax(1.0, fabs(theta)) || hnext == 0.0;
-            if (conv || j == kmax - 1) {
-                // x <- sum_i y_i V_i with V_0 = x / beta0 taken from x itself, then renormalised
-                const double2 y0 = cscale(sm.y[0], 1.0 / beta0);
-                count_flops_t<TB>(8.0 * (double)S * mm);
-                for (int64_t e = threadIdx.x; e < S; e += kThreads) {
-                    TB acc = czero<TB>();
-                    for (int i = 1; i < mm; ++i) cfma(acc, cT<TB>(sm.y[i]), V[(int64_t)i * smax + e]);
-                    x[e] = cT<TS>(cadd(cmul(y0, cd(x[e])), cd(acc)));
-                }
-                __syncthreads();
-                double2 nx = make_double2(0.0, 0.0);
-                for (int64_t e = threadIdx.x; e < S; e += kThreads) nx.x += cabs2(cd(x[e]));
-                const double inv = 1.0 / sqrt(block_sum(nx, sm).x);
-                for (int64_t e = threadIdx.x; e < S; e += kThreads) x[e] = cT<TS>(cscale(cd(x[e]), inv));
-                __syncthreads();
-                return conv ? 1 : 0;
-            }
-            const double inv = 1.0 / hnext;
-            for (int64_t e = threadIdx.x; e < S; e += kThreads) w[e] = cT<TB>(cscale(cd(w[e]), inv));
-            __syncthreads();
-            continue;
-        }
-        const long long te = sub_start();
-        small_expm(sm, mm, tau, herm != 0);
-        __syncthreads();
-        sub_stop(2, te);
-        const double err = hnext * sqrt(cabs2(sm.y[j]));
-        if (!isfinite(err)) return -1;
-        if (err <= tol || hnext == 0.0) {
-            const double2 y0 = sm.y[0];
-            count_flops_t<TB>(8.0 * (double)S * mm);
-            for (int64_t e = threadIdx.x; e < S; e += kThreads) {
-                TB acc = czero<TB>();
-                for (int i = 1; i < mm; ++i) cfma(acc, cT<TB>(sm.y[i]), V[(int64_t)i * smax + e]);
-                x[e] = cT<TS>(cadd(cmul(y0, cd(x[e])), cscale(cd(acc), beta0)));
-            }
-            __syncthreads();
-            return 1;
-        }
-        const double inv = 1.0 / hnext;
-        for (int64_t e = threadIdx.x; e < S; e += kThreads) w[e] = cT<TB>(cscale(cd(w[e]), inv));   // (kept exact in FP64 mode)
-        __syncthreads();
-    }
-    return 0;
-}
-
-template <class TS, class TB>
-__device__ int krylov_expm(TS* x, const Shape& sh, const TtnEntry* es, int ne, const TtnSlot* slots,
-                           double tau, int herm, double tol, int kmax, TB* V, int64_t smax, TB* t1, TB* t2,
-                           TB* t3, Smem& sm) {
-    // substeps: halve the interval whenever kmax is reached (at most 2^12 pieces)
-    int nsub = 1, done = 0;
-    while (done < nsub) {
-        const int r = krylov_once(x, sh, es, ne, slots, tau / nsub, herm, tol, kmax, V, smax, t1, t2, t3, sm);
-        if (r < 0) return 0;
-        if (r > 0) {
-            ++done;
-        } else {
-            if (nsub >= (1 << 12)) return 0;
-            nsub *= 2; done *= 2;
-        }
-    }
-    return 1;
-}
-
-// Lowest eigenpair of a Hermitian H_eff by restarted Lanczos (restart from
-// the current Ritz vector after kmax steps).  Returns 1 and the eigenvalue
-// on convergence, 0 otherwise.
-template <class TS, class TB>
-__device__ int krylov_ground(TS* x, const Shape& sh, const TtnEntry* es, int ne, const TtnSlot* slots, double tol,
-                             int kmax, TB* V, int64_t smax, TB* t1, TB* t2, TB* t3, Smem& sm, double* theta) {
-    for (int r = 0; r < 200; ++r) {
-        const int s = krylov_once(x, sh, es, ne, slots, 0.0, 1, tol, kmax, V, smax, t1, t2, t3, sm, 1);
-        if (s < 0) return 0;
-        if (s > 0) {
-            *theta = sm.u[0].x;
-            return 1;
-        }
-    }
-    return 0;
-}
-
-template <class TB, class TS>
-__device__ const TB* as_bulk(const TS* a, TB* buf, int64_t n) {
-    if (sizeof(TS) == sizeof(TB)) return (const TB*)a;
-    const long long t0 = sub_start();
-    for (int64_t i = threadIdx.x; i < n; i += kThreads) buf[i] = cT<TB>(cd(a[i]));
-    __syncthreads();
-    sub_stop(4, t0);
-    return buf;
-}
-
-
-// ---------------------------------------------------------------------------
-// Subspace expansion (paper Sec. II.D).
-// ---------------------------------------------------------------------------
-// Hermitian eigen-decomposition A = V diag(A') V^H of an n x n complex matrix
-// (FP64, row-major, in place: the diagonal of A holds the eigenvalues on
-// return) by the cyclic Jacobi method with the parallel round-robin pair
-// ordering: in each round n/2 disjoint (p, q) pairs are rotated at once.
-// Each rotation is G = diag(1, e^{-i phi}) times the real rotation that
-// annihilates the now real off-diagonal element (Golub & Van Loan, Sec. 8.5).
-__device__ void jacobi_eigh(double2* A, double2* Vm, int n, Smem& sm) {
-    const int tid = threadIdx.x;
-    for (int i = tid; i < n * n; i += kThreads) Vm[i] = make_double2(i / n == i % n ? 1.0 : 0.0, 0.0);
-    const int nn = (n + 1) & ~1;
-    const int npair = nn / 2;
-    double* rc = (double*)dyn_smem;
-    double* rs = rc + npair;
-    double2* ph = (double2*)(rs + npair);
-    int* pp = (int*)(ph + npair);
-    int* pq = pp + npair;
-    __syncthreads();
-    for (int sweep = 0; sweep < 60; ++sweep) {
-        double2 part = make_double2(0.0, 0.0);
-        for (int i = tid; i < n * n; i += kThreads) {
-            const int r = i / n, c = i - r * n;
-            if (r != c) part.x += cabs2(A[i]);
-            else part.y += A[i].x * A[i].x;
-        }
-        const double2 nrm = block_sum(part, sm);
-        if (nrm.x <= 1e-30 * (nrm.x + nrm.y) || nrm.x == 0.0) break;
-        for (int rnd = 0; rnd < nn - 1; ++rnd) {
-            for (int i = tid; i < npair; i += kThreads) {
-                const int a = (i == 0) ? 0 : ((i - 1 + rnd) % (nn - 1)) + 1;
-                const int jj = nn - 1 - i;
-                const int b = ((jj - 1 + rnd) % (nn - 1)) + 1;
-                const int p = min(a, b), q = max(a, b);
-                double c = 1.0, sn = 0.0;
-                double2 e = make_double2(1.0, 0.0);
-                if (q < n) {
-                    const double2 apq = A[p * n + q];
-                    const double r = sqrt(cabs2(apq));
-                    if (r > 1e-300) {
-                        const double theta = (A[q * n + q].x - A[p * n + p].x) / (2.0 * r);
-                        const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-                        c = 1.0 / sqrt(t * t + 1.0);
-                        sn = t * c;
-                        e = make_double2(apq.x / r, -apq.y / r);          // e^{-i phi}
-                    }
-                }
-                rc[i] = c; rs[i] = sn; ph[i] = e; pp[i] = p; pq[i] = q;
-            }
-            __syncthreads();
-            for (int idx = tid; idx < npair * n; idx += kThreads) {      // columns of A and V
-                const int i = idx / n, row = idx - (idx / n) * n;
-                const int p = pp[i], q = pq[i];
-                if (q >= n || rs[i] == 0.0) continue;
-                const double c = rc[i], sn = rs[i];
-                const double2 e = ph[i];
-                double2 ap = A[row * n + p], aq = cmul(e, A[row * n + q]);
-                A[row * n + p] = make_double2(c * ap.x - sn * aq.x, c * ap.y - sn * aq.y);
-                A[row * n + q] = make_double2(sn * ap.x + c * aq.x, sn * ap.y + c * aq.y);
-                ap = Vm[row * n + p]; aq = cmul(e, Vm[row * n + q]);
-                Vm[row * n + p] = make_double2(c * ap.x - sn * aq.x, c * ap.y - sn * aq.y);
-                Vm[row * n + q] = make_double2(sn * ap.x + c * aq.x, sn * ap.y + c * aq.y);
-            }
-            __syncthreads();
-            for (int idx = tid; idx < npair * n; idx += kThreads) {      // rows of A
-                const int i = idx / n, col = idx - (idx / n) * n;
-                const int p = pp[i], q = pq[i];
-                if (q >= n || rs[i] == 0.0) continue;
-                const double c = rc[i], sn = rs[i];
-                const double2 ec = make_double2(ph[i].x, -ph[i].y);     // e^{+i phi}
-                const double2 ap = A[p * n + col], aq = cmul(ec, A[q * n + col]);
-                A[p * n + col] = make_double2(c * ap.x - sn * aq.x, c * ap.y - sn * aq.y);
-                A[q * n + col] = make_double2(sn * ap.x + c * aq.x, sn * ap.y + c * aq.y);
-            }
-            __syncthreads();
-        }
-    }
-}
-
-// C = op(A) * B for small dense FP64 matrices (row-major): A is m x k (or
-// k x m when adjA, then conjugate-transposed), B is k x n.
-__device__ void small_gemm(double2* C, const double2* A, const double2* B, int m, int k, int n, bool adjA) {
-    for (int idx = threadIdx.x; idx < m * n; idx += kThreads) {
-        const int i = idx / n, j = idx - (idx / n) * n;
-        double2 acc = make_double2(0.0, 0.0);
-        for (int l = 0; l < k; ++l) {
-            const double2 a = adjA ? make_double2(A[l * m + i].x, -A[l * m + i].y) : A[i * k + l];
-            acc = cadd(acc, cmul(a, B[l * n + j]));
-        }
-        C[idx] = acc;
-    }
-    count_flops_t<double2>(8.0 * m * k * n);
-    __syncthreads();
-}
-
-// Test the bond to child c = children(z)[k] for new single-particle
-// functions (the centre is at z).  With X_a the child's up channel a applied
-// at the two-site level to A^c, W~_a = sum_b w_ab D_b A^z the matching down
-// channels applied to A^z, P_c = A^c A^c^dag and P_S the projector on the
-// child's single-hole functions (QR of A^z along k),
-//     Y = (1 - P_c) G (1 - P_S) = X' W'^T,  Y Y^dag = X' C X'^dag,
-// with X' = (1 - P_c) X, W' = (1 - Q_S Q_S^dag) W~, C = W'^T conj W'.  The
-// dominant eigenvectors of Y Y^dag are found in span X': with
-// E = X'^dag X' = V L V^dag and F = V L^{-1/2} (numerically nonzero part),
-// T = F^dag E C E F is Hermitian and its eigenvector w gives u = X' F w.
-template <class TS, class TB>
-__device__ void spawn_op(const TtnOp& op, const TtnInstance& in, Smem& sm, TB* V, int64_t smax, TB* t1, TB* t2,
-                         double2* Wc, double2* Qc) {
-    Shape shz, shc;
-    shz.D = op.D; shc.D = op.Dc;
-    for (int j = 0; j < TTN_MAXD; ++j) {
-        shz.d[j] = j < op.D ? op.dims[j] : 1;
-        shc.d[j] = j < op.Dc ? op.dimsc[j] : 1;
-    }
-    const int k = op.k;
-    const int chi = shz.d[k];
-    const int64_t Sz = shz.size(), Sc = shc.size();
-    const int NJ = (int)(Sc / chi), NT = (int)(Sz / chi);
-    int cap = min(in.chi_max, min(NJ, NT)) - chi;
-    if (cap <= 0 || in.spawn_eps <= 0.0) return;
-    if (cap > TTN_SPAWN_MAX_NEW) cap = TTN_SPAWN_MAX_NEW;
-    // distinct non-identity up channels among the bond terms
-    const TtnEntry* eb = in.entries + op.e2;
-    int ids[13];
-    int A = 0;
-    for (int i = 0; i < op.ne2; ++i) {
-        const int a = eb[i].slot[0];
-        if (a < 0) continue;
-        bool seen = false;
-        for (int q = 0; q < A; ++q) seen |= ids[q] == a;
-        if (!seen) {
-            if (A == 13) return;                 // too many channels for the workspace
-            ids[A++] = a;
-        }
-    }
-    const int K = A * chi;
-    if (A == 0 || K > in.spawn_kmax) return;
-    const TtnSlot* slots = in.slots;
-    TB* Mc = V;
-    TB* Mz = V + smax;
-    TB* X = V + 2 * smax;                       // A buffers of Sc
-    TB* Wt = V + (2 + A) * smax;                // A buffers of Sz
-    TB* Wb = V + (2 + 2 * A) * smax;
-    TB* Qsc = V + (3 + 2 * A) * smax;
-    TB* g = V + (4 + 2 * A) * smax;             // chi x chi scratch
-    double2* ws = (double2*)in.spawn_ws;
-    double2* Acopy = ws;
-    double2* E = ws + smax;
-    double2* Cm = E + (int64_t)K * K;
-    double2* T = Cm + (int64_t)K * K;
-    double2* VE = T + (int64_t)K * K;
-    double2* WT = VE + (int64_t)K * K;
-    double2* P1 = WT + (int64_t)K * K;
-    {
-        const TS* Ac = (const TS*)op.c;
-        const TS* Az = (const TS*)op.a;
-        for (int64_t i = threadIdx.x; i < Sc; i += kThreads) Mc[i] = cT<TB>(cd(Ac[i]));
-        for (int64_t i = threadIdx.x; i < Sz; i += kThreads) { Mz[i] = cT<TB>(cd(Az[i])); Acopy[i] = cd(Az[i]); }
-        __syncthreads();
-    }
-    const int lastc = shc.D - 1;
-    // X_a = (1 - Mc Mc^dag) U_a Mc
-    for (int a = 0; a < A; ++a) {
-        TB* Xa = X + a * smax;
-        for (int64_t i = threadIdx.x; i < Sc; i += kThreads) Xa[i] = czero<TB>();
-        __syncthreads();
-        const TtnEntry* eu = in.entries + op.e0;
-        for (int i = 0; i < op.ne; ++i) {
-            const TtnEntry e = eu[i];
-            if (e.out != ids[a]) continue;
-            bool any = false;
-            for (int m = 0; m < shc.D; ++m) any |= (m != lastc && e.slot[m] >= 0);
-            if (!any) {
-                const TB wt = cT<TB>(make_double2(e.wr, e.wi));
-                for (int64_t x = threadIdx.x; x < Sc; x += kThreads) { TB o = Xa[x]; cfma(o, wt, Mc[x]); Xa[x] = o; }
-                __syncthreads();
-            } else {
-                apply_chain((const TB*)Mc, t1, t2, shc, e, slots, lastc, Xa, make_double2(e.wr, e.wi));
-            }
-        }
-        for (int i = threadIdx.x; i < chi * chi; i += kThreads) g[i] = czero<TB>();
-        __syncthreads();
-        gram_acc(g, (const TB*)Mc, (const TB*)Xa, shc, lastc, make_double2(1.0, 0.0));
-        mode_prod(Xa, (const TB*)Mc, shc.before(lastc), chi, chi, (int64_t)1, (const TB*)g, true,
-                  make_double2(-1.0, 0.0), true);
-        __syncthreads();
-    }
-    // W~_a = sum_b w_ab D_b Mz
-    for (int a = 0; a < A; ++a) {
-        TB* Wa = Wt + a * smax;
-        for (int64_t i = threadIdx.x; i < Sz; i += kThreads) Wa[i] = czero<TB>();
-        __syncthreads();
-        for (int i = 0; i < op.ne2; ++i) {
-            const TtnEntry tb = eb[i];
-            if (tb.slot[0] != ids[a]) continue;
-            const int bsl = tb.slot[1];
-            const TB* src = Mz;
-            if (bsl >= 0) {
-                for (int64_t x = threadIdx.x; x < Sz; x += kThreads) Wb[x] = czero<TB>();
-                __syncthreads();
-                const TtnEntry* ed = in.entries + op.e1;
-                for (int q = 0; q < op.ne1; ++q) {
-                    const TtnEntry e = ed[q];
-                    if (e.out != bsl) continue;
-                    bool any = false;
-                    for (int m = 0; m < shz.D; ++m) any |= (m != k && e.slot[m] >= 0);
-                    if (!any) {
-                        const TB wt = cT<TB>(make_double2(e.wr, e.wi));
-                        for (int64_t x = threadIdx.x; x < Sz; x += kThreads) { TB o = Wb[x]; cfma(o, wt, Mz[x]); Wb[x] = o; }
-                        __syncthreads();
-                    } else {
-                        apply_chain((const TB*)Mz, t1, t2, shz, e, slots, k, Wb, make_double2(e.wr, e.wi));
-                    }
-                }
-                src = Wb;
-            }
-            const TB wt = cT<TB>(make_double2(tb.wr, tb.wi));
-            for (int64_t x = threadIdx.x; x < Sz; x += kThreads) { TB o = Wa[x]; cfma(o, wt, src[x]); Wa[x] = o; }
-            __syncthreads();
-        }
-    }
-    // single-hole functions: Q of A^z along k (FP64)
-    qr_mode(Acopy, shz, k, Wc, Qc, in.qtol, sm);
-    for (int64_t i = threadIdx.x; i < Sz; i += kThreads) Qsc[i] = cT<TB>(Acopy[i]);
-    __syncthreads();
-    // W'_a = (1 - Qs Qs^dag) W~_a   (G (1 - P_S) = X (W'^T) with P_S acting on rows of G)
-    for (int a = 0; a < A; ++a) {
-        TB* Wa = Wt + a * smax;
-        for (int i = threadIdx.x; i < chi * chi; i += kThreads) g[i] = czero<TB>();
-        __syncthreads();
-        gram_acc(g, (const TB*)Qsc, (const TB*)Wa, shz, k, make_double2(1.0, 0.0));
-        mode_prod(Wa, (const TB*)Qsc, shz.before(k), chi, chi, shz.after(k), (const TB*)g, true,
-                  make_double2(-1.0, 0.0), true);
-        __syncthreads();
-    }
-    // E = X'^dag X', C = conj(W'^dag W')   (K x K, FP64)
-    for (int a = 0; a < A; ++a)
-        for (int b = 0; b < A; ++b) {
-            for (int i = threadIdx.x; i < chi * chi; i += kThreads) g[i] = czero<TB>();
-            __syncthreads();
-            gram_acc(g, (const TB*)(X + a * smax), (const TB*)(X + b * smax), shc, lastc, make_double2(1.0, 0.0));
-            for (int i = threadIdx.x; i < chi * chi; i += kThreads)
-                E[(int64_t)(a * chi + i / chi) * K + b * chi + i % chi] = cd(g[i]);
-            __syncthreads();
-            for (int i = threadIdx.x; i < chi * chi; i += kThreads) g[i] = czero<TB>();
-            __syncthreads();
-            gram_acc(g, (const TB*)(Wt + a * smax), (const TB*)(Wt + b * smax), shz, k, make_double2(1.0, 0.0));
-            for (int i = threadIdx.x; i < chi * chi; i += kThreads) {
-                const double2 v = cd(g[i]);
-                Cm[(int64_t)(a * chi + i / chi) * K + b * chi + i % chi] = make_double2(v.x, -v.y);
-            }
-            __syncthreads();
-        }
-    // trace(Y Y^dag) = trace(C E) bounds every eigenvalue
-    const double thr = (in.spawn_eps / in.spawn_dt) * (in.spawn_eps / in.spawn_dt);
-    {
-        double2 part = make_double2(0.0, 0.0);
-        for (int64_t idx = threadIdx.x; idx < (int64_t)K * K; idx += kThreads) {
-            const int i = (int)(idx / K), j = (int)(idx % K);
-            part = cadd(part, cmul(Cm[(int64_t)i * K + j], E[(int64_t)j * K + i]));
-        }
-        const double tr = block_sum(part, sm).x;
-#ifdef TTN_SPAWN_DEBUG
-        if (threadIdx.x == 0) printf("spawn z=%d c=%d A=%d K=%d NJ=%d NT=%d trace=%.3e thr=%.3e\n", op.node, op.child, A, K, NJ, NT, tr, thr);
-#endif
-        if (!(tr >= thr)) return;
-    }
-    // E = V L V^dag; F = V L^{-1/2} on the numerically nonzero part (stored in P1, K x r)
-    for (int64_t i = threadIdx.x; i < (int64_t)K * K; i += kThreads) T[i] = E[i];
-    __syncthreads();
-    jacobi_eigh(T, VE, K, sm);
-    double lmax = 0.0;
-    for (int i = 0; i < K; ++i) lmax = fmax(lmax, T[(int64_t)i * K + i].x);
-    const double ltol = lmax * (sizeof(TB) == 16 ? 1e-13 : 1e-7);
-    int r = 0;
-    int* keep = (int*)(dyn_smem + 32768);
-    if (threadIdx.x == 0)
-        for (int i = 0; i < K; ++i)
-            if (T[(int64_t)i * K + i].x > ltol && lmax > 0.0) keep[r++] = i;
-    if (threadIdx.x == 0) sm.flag = r;
-    __syncthreads();
-    r = sm.flag;
-    __syncthreads();
-    if (r == 0) return;
-    for (int64_t idx = threadIdx.x; idx < (int64_t)K * r; idx += kThreads) {
-        const int i = (int)(idx / r), j = (int)(idx % r);
-        const int kj = keep[j];
-        P1[idx] = cscale(VE[(int64_t)i * K + kj], 1.0 / sqrt(T[(int64_t)kj * K + kj].x));
-    }
-    __syncthreads();
-    // T = F^dag E C E F  (r x r):  WT = E F (K x r), VE = C WT, T = WT^dag VE
-    small_gemm(WT, E, P1, K, K, r, false);
-    small_gemm(VE, Cm, WT, K, K, r, false);
-    small_gemm(T, WT, VE, r, K, r, true);
-    jacobi_eigh(T, Cm, r, sm);                 // eigenvectors of T in Cm (r x r)
-    // accept eigenvalues >= thr, largest first
-    int* order = keep + 256;
-    if (threadIdx.x == 0) {
-        int cnt = 0;
-        for (int i = 0; i < r; ++i) order[cnt++] = i;
-        for (int i = 0; i < cnt; ++i)
-            for (int j = i + 1; j < cnt; ++j)
-                if (T[(int64_t)order[j] * r + order[j]].x > T[(int64_t)order[i] * r + order[i]].x) {
-                    const int tmp = order[i]; order[i] = order[j]; order[j] = tmp;
-                }
-        int p = 0;
-        while (p < cnt && p < cap && T[(int64_t)order[p] * r + order[p]].x >= thr) ++p;
-        sm.flag = p;
-    }
-    __syncthreads();
-    const int p = sm.flag;
-    __syncthreads();
-    if (p == 0) return;
-    // coefficients g_i = F w_i (K x p) in E, then u_i = X' g_i (NJ x p, FP64) in the output
-    for (int64_t idx = threadIdx.x; idx < (int64_t)K * p; idx += kThreads) {
-        const int i = (int)(idx / p), j = (int)(idx % p);
-        double2 acc = make_double2(0.0, 0.0);
-        for (int l = 0; l < r; ++l) acc = cadd(acc, cmul(P1[(int64_t)i * r + l], Cm[(int64_t)l * r + order[j]]));
-        E[idx] = acc;
-    }
-    __syncthreads();
-    double* hdr = in.spawn_out;
-    double2* U = (double2*)(hdr + 4 + TTN_SPAWN_MAX_NEW);
-    for (int64_t idx = threadIdx.x; idx < (int64_t)NJ * p; idx += kThreads) {
-        const int J = (int)(idx % NJ), j = (int)(idx / NJ);
-        double2 acc = make_double2(0.0, 0.0);
-        for (int a = 0; a < A; ++a)
-            for (int n = 0; n < chi; ++n)
-                acc = cadd(acc, cmul(cd(X[a * smax + (int64_t)J * chi + n]), E[(int64_t)(a * chi + n) * p + j]));
-        U[idx] = acc;
-    }
-    __syncthreads();
-    // two Gram-Schmidt passes in FP64 against the existing functions and the earlier new ones
-    const TS* Ac = (const TS*)op.c;
-    for (int j = 0; j < p; ++j) {
-        double2* u = U + (int64_t)j * NJ;
-        for (int pass = 0; pass < 2; ++pass) {
-            for (int n = 0; n < chi + j; ++n) {
-                double2 part = make_double2(0.0, 0.0);
-                for (int J = threadIdx.x; J < NJ; J += kThreads) {
-                    const double2 b = n < chi ? cd(Ac[(int64_t)J * chi + n]) : U[(int64_t)(n - chi) * NJ + J];
-                    part = cadd(part, cconjmul(b, u[J]));
-                }
-                const double2 h = block_sum(part, sm);
-                for (int J = threadIdx.x; J < NJ; J += kThreads) {
-                    const double2 b = n < chi ? cd(Ac[(int64_t)J * chi + n]) : U[(int64_t)(n - chi) * NJ + J];
-                    u[J] = csub(u[J], cmul(h, b));
-                }
-                __syncthreads();
-            }
-        }
-        double2 part = make_double2(0.0, 0.0);
-        for (int J = threadIdx.x; J < NJ; J += kThreads) part.x += cabs2(u[J]);
-        const double nrm = sqrt(block_sum(part, sm).x);
-        for (int J = threadIdx.x; J < NJ; J += kThreads) u[J] = cscale(u[J], 1.0 / nrm);
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        hdr[0] = op.node; hdr[1] = op.child; hdr[2] = p; hdr[3] = NJ;
-        for (int j = 0; j < p; ++j) hdr[4 + j] = sqrt(fmax(0.0, T[(int64_t)order[j] * r + order[j]].x));
-        __threadfence();
-        atomicExch(in.status, TTN_STATUS_SPAWN_HIT);
-    }
-    __syncthreads();
-}
-
-// ---------------------------------------------------------------------------
-// interpreter: TS = node tensor / bond type, TB = bulk type
-// ---------------------------------------------------------------------------
-template <class TS, class TB>
-__device__ void run_op(const TtnOp& op, const TtnInstance& in, double dt, Smem& sm) {
-    Shape sh;
-    sh.D = op.D;
-    for (int j = 0; j < TTN_MAXD; ++j) sh.d[j] = j < op.D ? op.dims[j] : 1;
-    TB* work = (TB*)in.work;
-    TB* V = work;                                       // TTN_KMAX + 1 Krylov vectors
-    TB* t1 = work + (int64_t)(TTN_KMAX + 1) * in.smax;
-    TB* t2 = t1 + in.smax;
-    TB* t3 = t2 + in.smax;
-    double2* Wc = (double2*)(t3 + in.smax);
-    double2* Qc = Wc + in.smax;
-    const TtnEntry* es = in.entries + op.e0;
-    switch (op.type) {
-    case TTN_OP_QR_DOWN: {
-        TS* A = (TS*)op.a;
-        TS* B = (TS*)op.b;
-        qr_mode(A, sh, op.k, Wc, Qc, in.qtol, sm);
-        const int n = sh.d[op.k];
-        const int64_t m = sh.size() / n;
-        for (int i = threadIdx.x; i < n * n; i += kThreads) {   // B = R^T
-            const int a = i / n, b = i % n;
-            B[i] = cT<TS>(qr_R(Wc, m, b, a, sm));
-        }
-        __syncthreads();
-        break;
-    }
-    case TTN_OP_QR_UP: {
-        TS* A = (TS*)op.a;
-        TS* B = (TS*)op.b;
-        qr_mode(A, sh, op.k, Wc, Qc, in.qtol, sm);
-        const int n = sh.d[op.k];
-        const int64_t m = sh.size() / n;
-        for (int i = threadIdx.x; i < n * n; i += kThreads) {   // B = R
-            const int a = i / n, b = i % n;
-            B[i] = cT<TS>(qr_R(Wc, m, a, b, sm));
-        }
-        __syncthreads();
-        break;
-    }
-    case TTN_OP_ABSORB_CHILD: {      // A <- A x_last B^T
-        TS* A = (TS*)op.a;
-        const TS* B = (const TS*)op.b;
-        TS* tmp = (TS*)Qc;
-        const int n = sh.d[op.k];
-        mode_prod(tmp, A, sh.before(op.k), n, n, (int64_t)1, B, true, make_double2(1.0, 0.0), false);
-        __syncthreads();
-        copy_vec(A, (const TS*)tmp, sh.size());
-        __syncthreads();
-        break;
-    }
-    case TTN_OP_ABSORB_PARENT: {     // A <- B x_k A
-        TS* A = (TS*)op.a;
-        const TS* B = (const TS*)op.b;
-        TS* tmp = (TS*)Qc;
-        const int n = sh.d[op.k];
-        mode_prod(tmp, A, sh.before(op.k), n, n, sh.after(op.k), B, false, make_double2(1.0, 0.0), false);
-        __syncthreads();
-        copy_vec(A, (const TS*)tmp, sh.size());
-        __syncthreads();
-        break;
-    }
-    case TTN_OP_ENV: {                // Krylov vectors are free here: V[0] holds Q, V[1] the chain sum
-        const TB* Q = as_bulk<TB>((const TS*)op.a, V, sh.size());
-        env_build(Q, t1, t2, V + in.smax, sh, op.k, es, op.ne, in.slots);
-        break;
-    }
-    case TTN_OP_COMBO:
-        combo<TB>(es, op.ne, in.slots);
-        break;
-    case TTN_OP_EVOLVE: {
-        const int ok = krylov_expm((TS*)op.a, sh, es, op.ne, in.slots, op.tau_coef * dt, op.hermitian, in.ktol,
-                                   in.kmax, V, in.smax, t1, t2, t3, sm);
-        if (!ok && threadIdx.x == 0) atomicExch(in.status, 4);   // TTN_E_NOCONV
-        __syncthreads();
-        break;
-    }
-    case TTN_OP_EIGEN: {
-        // residual tolerance: FP64 rounding allows ~1e-12 relative; an FP32 Krylov basis ~1e-7
-        const double etol = sizeof(TB) == 16 ? fmax(in.ktol, 1e-12) : fmax(in.ktol, 1e-7);
-        double theta = 0.0;
-        const int ok = krylov_ground((TS*)op.a, sh, es, op.ne, in.slots, etol, in.kmax, V, in.smax, t1, t2, t3, sm,
-                                     &theta);
-        if (!ok && threadIdx.x == 0) atomicExch(in.status, 4);   // TTN_E_NOCONV
-        if (ok && threadIdx.x == 0 && op.out) op.out[0] = theta;
-        __syncthreads();
-        break;
-    }
-    case TTN_OP_DOT: {
-        double2 r;
-        if (op.ne > 0) {
-            const TB* A = as_bulk<TB>((const TS*)op.a, V, sh.size());
-            heff_apply(t1, A, t2, V + in.smax, t3, sh, es, op.ne, in.slots);
-            r = block_dot(A, t1, sh.size(), sm);
-        } else {
-            const TS* A = (const TS*)op.a;
-            r = block_dot(A, A, sh.size(), sm);
-        }
-        if (threadIdx.x == 0) { op.out[0] = r.x; op.out[1] = r.y; }
-        __syncthreads();
-        break;
-    }
-    case TTN_OP_CONTRACT_VEC: {      // chain of rectangular mode products, result into slot k
-        const TtnEntry e = es[0];
-        const TB* cur = as_bulk<TB>((const TS*)op.a, t3, sh.size());   // t3 is not a chain buffer here
-        Shape s2 = sh;
-        for (int j = 0; j < sh.D; ++j) {
-            if (e.slot[j] < 0) continue;
-            const TtnSlot s = in.slots[e.slot[j]];
-            TB* dst = (cur == t1) ? t2 : t1;
-            mode_prod(dst, cur, s2.before(j), s.cols, s.rows, s2.after(j), (const TB*)s.ptr, false,
-                      make_double2(1.0, 0.0), false);
-            __syncthreads();
-            s2.d[j] = s.rows;
-            cur = dst;
-        }
-        copy_vec((TB*)in.slots[op.k].ptr, cur, s2.size());
-        __syncthreads();
-        break;
-    }
-    case TTN_OP_SPAWN:
-        spawn_op<TS, TB>(op, in, sm, V, in.smax, t1, t2, Wc, Qc);
-        break;
-    case TTN_OP_STEP_END:
-        if (threadIdx.x == 0) {
-            const int s = *in.steps_done;
-            if (in.stamps) {
-                unsigned long long t;
-                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-                in.stamps[s & 4095] = t;
-            }
-            *in.steps_done = s + 1;
-        }
-        __syncthreads();
-        break;
-    default:
-        if (threadIdx.x == 0) atomicExch(in.status, 6);
-        __syncthreads();
-        break;
-    }
-}
-
-__device__ __forceinline__ long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return (long long)t;
-}
-
-// One thread block per instance runs its op list nrep times (nrep < 0: the
-// instance's own count and time step).  With a slice of device time > 0 a
-// block stops after the step that ends its slice; rep_out (optional)
-// receives, per block, the steps run, the status word and the elapsed time.
-// hdr (optional, device memory) supplies the instance count and the slice.
-template <class TS, class TB>
-__global__ void __launch_bounds__(kThreads, 2) program_kernel(const TtnInstance* insts, const TtnLaunchHdr* hdr,
-                                                              int n_inst, double dt, int nrep, long long slice_arg,
-                                                              TtnRepOut* rep_out) {
-    __shared__ Smem sm;
-    __shared__ int s_stop;
-    __shared__ long long s_t0;
-    const int b = blockIdx.x;
-    const int n = hdr ? hdr->n : n_inst;
-    const long long slice_ns = hdr ? hdr->slice_ns : slice_arg;
-    if (b >= n) return;
-    const TtnInstance in = insts[b];
-    const double dtb = nrep < 0 ? in.dt : dt;
-    const int nr = nrep < 0 ? in.nrep : nrep;
-    if (threadIdx.x == 0) {
-        s_flops = 0.0;
-        s_flops64 = 0.0;
-        for (int i = 0; i < 8; ++i) s_sub[i] = 0;
-        s_t0 = global_ns();
-        s_stop = 0;
-    }
-    __syncthreads();
-    int rep = 0;
-    while (rep < nr) {
-        for (int o = 0; o < in.n_ops; ++o) {
-            if (threadIdx.x == 0) sm.flag = *((volatile int*)in.status);
-            __syncthreads();
-            if (sm.flag != 0) break;
-            const TtnOp op = in.ops[o];
-            const long long c0 = clock64();
-            run_op<TS, TB>(op, in, dtb, sm);
-            if (threadIdx.x == 0 && in.op_cycles) atomicAdd(&in.op_cycles[op.type & 15], (unsigned long long)(clock64() - c0));
-        }
-        if (sm.flag != 0) break;
-        ++rep;
-        if (slice_ns > 0) {
-            if (threadIdx.x == 0) s_stop = global_ns() - s_t0 >= slice_ns;
-            __syncthreads();
-            if (s_stop) break;
-        }
-    }
-    if (threadIdx.x == 0 && in.flops) {
-        atomicAdd(in.flops, s_flops);
-        atomicAdd(in.flops + 1, s_flops64);
-    }
-    if (threadIdx.x == 0 && in.op_cycles)
-        for (int i = 0; i < 8; ++i) atomicAdd(&in.op_cycles[16 + i], s_sub[i]);
-    if (threadIdx.x == 0 && rep_out) {
-        TtnRepOut r;
-        r.reps = rep;
-        r.status = *((volatile int*)in.status);
-        r.elapsed_ns = global_ns() - s_t0;
-        rep_out[b] = r;
-    }
-}
-
 // One thread block applies a sum-of-products operator to one tensor (the
 // same device routine the sweep runs inside its Krylov exponentials).
-__global__ void __launch_bounds__(kThreads, 1) heff_kernel(const TtnEntry* es, int ne, const TtnSlot* slots, int D,
-                                                           Shape sh, const double2* x, double2* y, double2* t1,
-                                                           double2* t2, double2* t3) {
-    if (threadIdx.x == 0) { s_flops = 0.0; s_flops64 = 0.0; }
+__global__ void __launch_bounds__(256, 1) heff_kernel(const TtnEntry* es, int ne, const TtnSlot* slots, Shape sh,
+                                                      const double2* x, double2* y, double2* t1, double2* t2,
+                                                      double2* t3) {
+    if (threadIdx.x == 0) { s_flops = 0.0; s_flops64 = 0.0; s_count = 1; }
     __syncthreads();
-    (void)D;
-    heff_apply(y, x, t1, t2, t3, sh, es, ne, slots);
+    heff_apply(y, x, t1, t2, t3, sh, es, ne, slots, Solo<256>());
+}
+
+// The dynamic shared-memory attribute is per device: set once per device,
+// under a lock, remembered only after it succeeded.
+int heff_init() {
+    static std::mutex mu;
+    static bool done[256] = {false};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return (int)e;
+    if (dev < 0 || dev >= 256) return (int)cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[dev]) return 0;
+    e = cudaFuncSetAttribute(heff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kStageBytes);
+    if (e != cudaSuccess) return (int)e;
+    done[dev] = true;
+    return 0;
 }
 
 }  // namespace
 
 int ttn_launch_heff(const TtnEntry* d_entries, int ne, const TtnSlot* d_slots, int D, const int* dims,
                     const void* x, void* y, void* t1, void* t2, void* t3, cudaStream_t s) {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(heff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kStageBytes);
-        attr_set = true;
-    }
+    int e = heff_init();
+    if (e) return e;
     Shape sh;
     sh.D = D;
     for (int j = 0; j < TTN_MAXD; ++j) sh.d[j] = j < D ? dims[j] : 1;
-    heff_kernel<<<1, kThreads, kStageBytes, s>>>(d_entries, ne, d_slots, D, sh, (const double2*)x, (double2*)y,
-                                                 (double2*)t1, (double2*)t2, (double2*)t3);
+    heff_kernel<<<1, 256, kStageBytes, s>>>(d_entries, ne, d_slots, sh, (const double2*)x, (double2*)y,
+                                            (double2*)t1, (double2*)t2, (double2*)t3);
     return (int)cudaGetLastError();
 }
 
 int ttn_program_init() {
-    static std::once_flag once;
-    static cudaError_t err = cudaSuccess;
-    std::call_once(once, [] {
-        err = cudaFuncSetAttribute(program_kernel<double2, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStageBytes);
-        if (err == cudaSuccess)
-            err = cudaFuncSetAttribute(program_kernel<double2, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStageBytes);
-    });
-    return (int)err;
+    int e = ttn_variant_f64_solo_init();
+    if (!e) e = ttn_variant_mix_solo_init();
+    if (!e) e = ttn_variant_f64_clu_init();
+    if (!e) e = ttn_variant_mix_clu_init();
+    return e;
 }
 
-int ttn_launch_program(int precision, const TtnInstance* d_insts, int n_inst, double dt, int nrep, cudaStream_t s) {
-    return ttn_launch_program_ex(precision, d_insts, nullptr, n_inst, dt, nrep, 0, nullptr, s);
+int ttn_cluster_capacity(int precision, int cluster, int* max_active) {
+    return precision == 0 ? ttn_variant_f64_clu_capacity(cluster, max_active)
+                          : ttn_variant_mix_clu_capacity(cluster, max_active);
 }
 
-int ttn_launch_program_ex(int precision, const TtnInstance* d_insts, const TtnLaunchHdr* d_hdr, int grid, double dt,
-                          int nrep, long long slice_ns, TtnRepOut* d_rep_out, cudaStream_t s) {
-    if (grid <= 0) return 0;
-    int e = ttn_program_init();
-    if (e) return e;
-    if (precision == 0)
-        program_kernel<double2, double2><<<grid, kThreads, kStageBytes, s>>>(d_insts, d_hdr, grid, dt, nrep, slice_ns, d_rep_out);
-    else
-        program_kernel<double2, float2><<<grid, kThreads, kStageBytes, s>>>(d_insts, d_hdr, grid, dt, nrep, slice_ns, d_rep_out);
-    return (int)cudaGetLastError();
+int ttn_launch_program(int precision, int cluster, const TtnInstance* d_insts, int n_inst, double dt, int nrep,
+                       cudaStream_t s) {
+    return ttn_launch_program_ex(precision, cluster, d_insts, nullptr, n_inst, dt, nrep, 0, nullptr, s);
+}
+
+int ttn_launch_program_ex(int precision, int cluster, const TtnInstance* d_insts, const TtnLaunchHdr* d_hdr,
+                          int n_inst, double dt, int nrep, long long slice_ns, TtnRepOut* d_rep_out, cudaStream_t s) {
+    if (n_inst <= 0) return 0;
+    TtnVariantArgs a{d_insts, d_hdr, n_inst, cluster, dt, nrep, slice_ns, d_rep_out, s};
+    if (cluster <= 1) return precision == 0 ? ttn_variant_f64_solo(a) : ttn_variant_mix_solo(a);
+    return precision == 0 ? ttn_variant_f64_clu(a) : ttn_variant_mix_clu(a);
 }
 
 // ---------------------------------------------------------------------------

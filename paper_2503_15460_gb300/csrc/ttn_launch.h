@@ -1,26 +1,38 @@
-// Launch wrappers exported by ttn_kernels.cu to the host library.
+// Launch wrappers exported by the device translation units to the host library.
 #pragma once
 #include <cuda_runtime.h>
 
 #include "ttn_program.h"
 
-// Run the op list of each instance (one thread block per instance) nrep times.
+// Largest thread-block cluster one instance may use (non-portable size,
+// enabled per kernel).
+#define TTN_MAX_CLUSTER 16
+
+// Run the op list of each instance nrep times.  cluster <= 1: one thread
+// block (256 threads) per instance; cluster = 2..16: one thread-block
+// cluster of that many blocks (512 threads each) per instance.
 // precision: 0 = complex128, 1 = complex64 bulk.  Returns a cudaError_t code.
-int ttn_launch_program(int precision, const TtnInstance* d_insts, int n_inst, double dt, int nrep,
+int ttn_launch_program(int precision, int cluster, const TtnInstance* d_insts, int n_inst, double dt, int nrep,
                        cudaStream_t stream);
 
-// General form: `grid` blocks.  With d_hdr (device memory) the first
-// d_hdr->n blocks run and d_hdr->slice_ns replaces slice_ns; without it all
-// `grid` blocks run.  nrep < 0 takes each instance's own step count and
-// time step (TtnInstance::nrep, ::dt).  slice_ns > 0 ends a block after the
-// step that uses up its slice of device time.  d_rep_out (optional, `grid`
-// entries) receives what each block did.
-int ttn_launch_program_ex(int precision, const TtnInstance* d_insts, const TtnLaunchHdr* d_hdr, int grid, double dt,
-                          int nrep, long long slice_ns, TtnRepOut* d_rep_out, cudaStream_t stream);
+// General form: `n_inst` instances (grid n_inst x cluster blocks).  With
+// d_hdr (device memory) the first d_hdr->n instances run and
+// d_hdr->slice_ns replaces slice_ns; without it all `n_inst` run.  nrep < 0
+// takes each instance's own step count and time step (TtnInstance::nrep,
+// ::dt).  slice_ns > 0 ends an instance after the step that uses up its
+// slice of device time.  d_rep_out (optional, `n_inst` entries) receives
+// what each instance did.
+int ttn_launch_program_ex(int precision, int cluster, const TtnInstance* d_insts, const TtnLaunchHdr* d_hdr,
+                          int n_inst, double dt, int nrep, long long slice_ns, TtnRepOut* d_rep_out,
+                          cudaStream_t stream);
 
-// Set the kernel attributes once per process (call before capturing a
-// launch into a CUDA graph).  Returns a cudaError_t code.
+// Set the kernel attributes of every variant on the current device (call
+// before capturing a launch into a CUDA graph).  Returns a cudaError_t code.
 int ttn_program_init();
+
+// How many clusters of `cluster` blocks the cluster kernel of `precision`
+// can keep resident at once on the current device (0 if none).
+int ttn_cluster_capacity(int precision, int cluster, int* max_active);
 
 // Apply a sum-of-products operator (entries, factor slots) to the complex128
 // tensor x (dims[0..D-1]) into y with one thread block; t1..t3 are scratch
@@ -40,3 +52,27 @@ int ttn_launch_heff(const TtnEntry* d_entries, int ne, const TtnSlot* d_slots, i
 // device array (host tables are copied into it on `stream`).
 int ttn_launch_heff_noalloc(const TtnEntry* h_entries, int ne, const TtnSlot* h_slots, int n_slots, int D,
                             const int* dims, const void* x, void* y, cudaStream_t stream);
+
+// ---- internal: one entry point per kernel variant (own translation unit) ----
+struct TtnVariantArgs {
+    const TtnInstance* insts;
+    const TtnLaunchHdr* hdr;
+    int n_inst;
+    int cluster;
+    double dt;
+    int nrep;
+    long long slice_ns;
+    TtnRepOut* rep_out;
+    cudaStream_t stream;
+};
+int ttn_variant_f64_solo(const TtnVariantArgs& a);
+int ttn_variant_mix_solo(const TtnVariantArgs& a);
+int ttn_variant_f64_clu(const TtnVariantArgs& a);
+int ttn_variant_mix_clu(const TtnVariantArgs& a);
+// attribute set-up (init) and cluster occupancy (capacity) of one variant
+int ttn_variant_f64_solo_init();
+int ttn_variant_mix_solo_init();
+int ttn_variant_f64_clu_init();
+int ttn_variant_mix_clu_init();
+int ttn_variant_f64_clu_capacity(int cluster, int* max_active);
+int ttn_variant_mix_clu_capacity(int cluster, int* max_active);

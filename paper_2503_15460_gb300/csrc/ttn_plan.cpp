@@ -1000,7 +1000,7 @@ std::string make_plan(const Tree& t, const Hamiltonian* h, int precision, Plan& 
                 if (p.entries[rg.first + i].slot[0] >= 0) ids.insert(p.entries[rg.first + i].slot[0]);
             kmax = std::max(kmax, (int)ids.size() * t.bond[c]);
         }
-        p.spawn_kmax = std::min(kmax, 256);
+        p.spawn_kmax = std::min(kmax, TTN_SPAWN_MAX_K);
         p.spawn_ws_off = p.total_bytes;
         p.total_bytes = align_up(p.total_bytes + 16 * (p.smax + 6 * (int64_t)p.spawn_kmax * p.spawn_kmax), 256);
         OpSpec s;

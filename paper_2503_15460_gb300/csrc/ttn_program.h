@@ -39,7 +39,15 @@ enum TtnOpType : int {
 // Status word value left by a SPAWN op that accepted new single-particle
 // functions: the program stops so that the host can grow the bond.
 #define TTN_STATUS_SPAWN_HIT 100
-#define TTN_SPAWN_MAX_NEW 16
+// Status word value of a SPAWN op whose bond has more up channels (or a
+// larger channel space K = channels x bond dimension) than its workspace.
+#define TTN_STATUS_SPAWN_SPACE 7
+// Functions one growth may add to a bond: every accepted one up to the cap
+// chi_max (Sec. II.D), so at most the largest bond dimension.
+#define TTN_SPAWN_MAX_NEW TTN_MAXCHI
+// Largest channel count and channel space K of one bond in a SPAWN op.
+#define TTN_SPAWN_MAX_CHANNELS 32
+#define TTN_SPAWN_MAX_K 512
 
 struct TtnEntry {
     double wr, wi;          // complex weight

@@ -100,7 +100,7 @@ ttn_status issue(ttn_server* s) {
                         s->run_stream), "table upload");
     SCK(cudaMemcpyAsync(s->d_hdr, s->h_hdr, sizeof(TtnLaunchHdr), cudaMemcpyHostToDevice, s->run_stream),
         "header upload");
-    int e = ttn_launch_program_ex(s->precision, s->d_table, s->d_hdr, s->max_slots, 0.0, -1, 0, s->d_rep,
+    int e = ttn_launch_program_ex(s->precision, 1, s->d_table, s->d_hdr, s->max_slots, 0.0, -1, 0, s->d_rep,
                                   s->run_stream);
     if (e) return srv_cuda(s, (cudaError_t)e, "kernel launch");
     SCK(cudaMemcpyAsync(s->h_rep, s->d_rep, sizeof(TtnRepOut) * s->max_slots, cudaMemcpyDeviceToHost,
@@ -282,6 +282,8 @@ ttn_status ttn_server_submit(ttn_server* s, ttn_ctx* ctx, double dt, int nsteps,
         if (opts->expand) return srv_fail(s, TTN_E_INVALID, "the server runs fixed bond dimensions (expand = 0)");
         if (opts->krylov_maxdim > TTN_KMAX) return srv_fail(s, TTN_E_INVALID, "krylov_maxdim must be <= 32");
     }
+    if (ctx->plan.max_chi > ttn::kSoloMaxDim)
+        return srv_fail(s, TTN_E_INVALID, "the server runs one thread block per request: index dimensions must be <= 45");
     for (const Request& r : s->queue)
         if (r.ctx == ctx) return srv_fail(s, TTN_E_INVALID, "context already submitted");
     for (const Request& r : s->running)

@@ -74,6 +74,8 @@ _sig = {
     "ttn_tree": ([_P, C.POINTER(C.c_int), C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "ttn_set_stream": ([_P, _P], C.c_int),
     "ttn_set_device": ([C.c_int], C.c_int),
+    "ttn_set_cluster": ([_P, C.c_int], C.c_int),
+    "ttn_get_cluster": ([_P, C.POINTER(C.c_int)], C.c_int),
     "ttn_heff_apply": ([_P, C.c_int, _I32, C.c_int, _C128, _I32, C.c_int, C.POINTER(_P), _P, _P], C.c_int),
     "ttn_heff_apply_noalloc": ([_P, C.c_int, _I32, C.c_int, _C128, _I32, C.c_int, C.POINTER(_P), _P, _P], C.c_int),
     "ttn_op_cycles": ([_P, np.ctypeslib.ndpointer(dtype=np.uint64, flags="C_CONTIGUOUS")], C.c_int),
@@ -323,6 +325,16 @@ def ttn_set_device(device: int):
     _check(_lib.ttn_set_device(int(device)), None)
 
 
+def ttn_set_cluster(ctx, blocks: int):
+    _check(_lib.ttn_set_cluster(ctx, int(blocks)), ctx)
+
+
+def ttn_get_cluster(ctx) -> int:
+    n = C.c_int(0)
+    _check(_lib.ttn_get_cluster(ctx, C.byref(n)), ctx)
+    return n.value
+
+
 def ttn_step_stats(ctx, max_stamps=4096):
     steps = C.c_int64(0)
     fl = C.c_double(0.0)
@@ -502,6 +514,13 @@ class Context:
 
     def step(self, dt, nsteps=1, opts=None):
         ttn_step(self.h, dt, nsteps, opts)
+
+    def set_cluster(self, blocks):
+        """Thread blocks per instance: 0 = automatic, 1 = one block, 2..16 = a cluster."""
+        ttn_set_cluster(self.h, blocks)
+
+    def cluster(self):
+        return ttn_get_cluster(self.h)
 
     def set_coefficients(self, coeff):
         ttn_set_coefficients(self.h, coeff)
