@@ -200,6 +200,9 @@ def run_ours(args, rank, world, local_rank):
             import torch.distributed as dist
             dist.barrier()
 
+    # measured pipe peaks of this device (roofline denominators)
+    peaks = ttn.ttn_pipe_peaks(stream.cuda_stream, 0.5)
+
     # ---- mixed precision, batched: the headline ------------------------------
     ctxs = make_ctxs(ttn.TTN_MIXED)
     handles = [c.h for c in ctxs]
@@ -303,23 +306,30 @@ def run_ours(args, rank, world, local_rank):
     for c in ctxs:
         c.close()
     return dict(ms=ms, value=value, flops_per_step=float(flops_per_step), flops64_per_step=float(flops64_per_step),
-                lat=lat, clocks=clocks, fp64=fp64, e2e=e2e, batch_bytes=batch_bytes)
+                lat=lat, clocks=clocks, fp64=fp64, e2e=e2e, batch_bytes=batch_bytes, peaks=peaks)
 
 
-def alu_roofline(flops, flops64, seconds, traffic):
-    """Per-pipe utilisation of one step: FP32 work against the FP32 lanes,
-    FP64 work against the FP64 lanes; the pipe with the larger lower bound
-    on time is the one that binds."""
+def alu_roofline(flops, flops64, seconds, traffic, peaks=None):
+    """Per-pipe utilisation of one step: FP32 work against the FP32 pipe,
+    FP64 work against the FP64 pipe; the pipe with the larger lower bound
+    on time is the one that binds.  peaks = (fp32, fp64) TFLOP/s measured in
+    this run by the FMA-throughput kernels (ttn_pipe_peaks); else the unit
+    counts at the maximum clock."""
     f32 = flops - flops64
     a32, a64 = f32 / seconds / 1e12, flops64 / seconds / 1e12
-    pipes = {"fp32": {"achieved": a32, "peak": PEAK_FP32, "frac": a32 / PEAK_FP32, "flops_per_step": f32},
-             "fp64": {"achieved": a64, "peak": PEAK_FP64, "frac": a64 / PEAK_FP64, "flops_per_step": flops64}}
+    p32, p64 = peaks if peaks else (PEAK_FP32, PEAK_FP64)
+    pipes = {"fp32": {"achieved": a32, "peak": p32, "frac": a32 / p32, "flops_per_step": f32,
+                      "nominal_peak": PEAK_FP32},
+             "fp64": {"achieved": a64, "peak": p64, "frac": a64 / p64, "flops_per_step": flops64,
+                      "nominal_peak": PEAK_FP64}}
     bind = max(pipes, key=lambda k: pipes[k]["frac"])
     b = pipes[bind]
+    src = ("measured in this run: FP32 / FP64 fused multiply-add throughput of a kernel filling every SM with "
+           "independent FMA chains (ttn_pipe_peaks, CUDA events), fractions are of measured") if peaks else (
+           f"derived: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 / {FP64_LANES_PER_SM} FP64 lanes x 2 flop x "
+           f"{SM_MAX_MHZ:.0f} MHz")
     return {"bound": "alu", "pipe": bind, "achieved": b["achieved"], "peak": b["peak"], "unit": "TFLOP/s",
-            "frac": b["frac"], "traffic": traffic,
-            "peak_source": (f"derived: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 / {FP64_LANES_PER_SM} FP64 lanes "
-                            f"x 2 flop x {SM_MAX_MHZ:.0f} MHz (the measured peaks hold no FP32 / FP64 entry)"),
+            "frac": b["frac"], "traffic": traffic, "peak_source": src,
             "pipes": pipes, "flops_per_step": flops}
 
 
@@ -405,30 +415,104 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------------------
+# accuracy of the mixed form over long horizons (separate JSON line)
+# ---------------------------------------------------------------------------
+ACCURACY_WORKLOADS = ("vibronic", "heom", "spinboson300")
+
+
+def accuracy_problems(workload, n):
+    import workloads as W
+    if workload == "heom":
+        return [W.config_c4(lam=0.1 * (1.0 + 0.25 * i)) for i in range(n)]
+    if workload == "spinboson300":
+        return [W.config_c3(alpha=a) for a in (0.1, 0.5)[:n]]
+    return [W.config_c2(seed=2 + i) for i in range(n)]
+
+
+def accuracy_observables(ctx, p, workload):
+    """Vibronic / spin-boson: every leaf's populations; HEOM: the reduced
+    density matrix of the system (all four elements of vec rho_S)."""
+    if workload == "heom":
+        return np.asarray(ctx.vacuum_projection(p.meta["sys"]))
+    return np.concatenate(ctx.populations(p.obs_leaves))
+
+
+def run_accuracy(args):
+    """Mixed against complex128 on the GPU over a configuration's horizon:
+    both arms batched (one launch per interval and precision), each instance
+    on a 16-block cluster; the largest observable difference is recorded
+    every `--acc-every` steps."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2503_15460_gb300 import ttn
+    ttn.ttn_set_device(0)
+    wl = args.workload
+    probs = accuracy_problems(wl, args.acc_instances)
+    dt = probs[0].dt
+    steps = args.acc_steps or probs[0].nsteps
+
+    def ctxs(precision):
+        out = []
+        for p in probs:
+            c = ttn.Context(p.tree, precision)
+            c.set_cluster(args.acc_cluster)
+            c.set_state(p.tensors)
+            c.set_hamiltonian(p.H)
+            out.append(c)
+        return out
+
+    c64, cmx = ctxs(ttn.TTN_FP64), ctxs(ttn.TTN_MIXED)
+    curve, done, t64, tmx = [], 0, 0.0, 0.0
+    while done < steps:
+        k = min(args.acc_every, steps - done)
+        t0 = time.perf_counter()
+        ttn.ttn_step_batch([c.h for c in c64], dt, k)
+        t1 = time.perf_counter()
+        ttn.ttn_step_batch([c.h for c in cmx], dt, k)
+        t2 = time.perf_counter()
+        t64 += t1 - t0
+        tmx += t2 - t1
+        done += k
+        err = max(float(np.abs(accuracy_observables(a, p, wl) - accuracy_observables(b, p, wl)).max())
+                  for a, b, p in zip(cmx, c64, probs))
+        curve.append([done, err])
+        print(f"[accuracy] {wl} step {done}: max |mixed - fp64| = {err:.3e}", file=sys.stderr, flush=True)
+    norms = [float(c.norm_energy()[0]) for c in c64]
+    for c in c64 + cmx:
+        c.close()
+    line = {"metric": "max |observable(mixed) - observable(complex128)| over the horizon, GPU",
+            "workload": wl, "instances": [p.name for p in probs], "dt": dt, "steps": steps,
+            "observable": "vec rho_S of the system" if wl == "heom" else "populations of every leaf",
+            "max_err": max(e for _, e in curve), "curve": curve, "cluster_blocks": args.acc_cluster,
+            "seconds_fp64": t64, "seconds_mixed": tmx, "fp64_norm_end": norms}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
 # serving stream (continuous batching through ttn_server)
 # ---------------------------------------------------------------------------
 SERVE_RANGES = dict(n_modes_range=(8, 64), d_range=(8, 20), chi_range=(4, 12), steps_range=(10, 40))
+# the serving leg of the default run: the same recipe, fewer requests and steps
+SERVE_RANGES_DEFAULT = dict(n_modes_range=(8, 48), d_range=(8, 20), chi_range=(4, 12), steps_range=(6, 20))
 
 
-def serve_workload_name(n):
-    r = SERVE_RANGES
+def serve_workload_name(n, ranges):
+    r = ranges
     return (f"{n} seeded requests, half spin-boson (dt 0.05, alpha U[0.05,1], beta in {{inf,5,1}}) and half "
             f"two-state vibronic (dt 0.1), balanced binary trees, modes {r['n_modes_range']}, local dims "
             f"{r['d_range']}, bond dims {r['chi_range']}, steps {r['steps_range']}")
 
 
-def run_serving(args):
-    """Serving stream: all requests at t0 (burst), then Poisson arrivals at
-    80 % of the burst's measured capacity; reference: requests one at a time
-    in FP64 on a sample, extrapolated by step count."""
-    import torch
-    torch.cuda.set_device(0)
-    from paper_2503_15460_gb300 import ttn
-    import workloads as W
-    ttn.ttn_set_device(0)
-    reqs = W.config_c5_requests(args.serve_requests, seed=5, **SERVE_RANGES)
+def serve_stream(ttn, W, n_requests, ranges, slice_ms, burst=True, sample=8, sample_steps=3, log=None):
+    """Continuous batching of a seeded request stream through ttn_server:
+    optionally all requests at t0 (burst), then Poisson arrivals at 80 % of
+    the measured capacity; the reference runs a sample of the requests one
+    at a time in FP64 (ttn_step)."""
+    reqs = W.config_c5_requests(n_requests, seed=5, **ranges)
     probs = [W.c5_problem(r) for r in reqs]
     total_steps = sum(p.nsteps for p in probs)
+    log = log or (lambda m: None)
 
     def contexts(precision):
         cs = []
@@ -441,7 +525,7 @@ def run_serving(args):
 
     def run(arrivals):
         ctxs = contexts(ttn.TTN_MIXED)
-        srv = ttn.Server(ttn.TTN_MIXED, slice_ms=args.slice_ms)
+        srv = ttn.Server(ttn.TTN_MIXED, slice_ms=slice_ms)
         order = np.argsort(arrivals, kind="stable")
         t_arr, t_done, tick = {}, {}, {}
         nxt = 0
@@ -472,48 +556,73 @@ def run_serving(args):
                 "launches": st["launches"], "peak_running": st["peak_running"],
                 "peak_bytes": st["peak_bytes"]}
 
-    def log(msg):
-        print(f"[serve] {msg}", file=sys.stderr, flush=True)
-
     log(f"{len(probs)} requests, {total_steps} steps")
-    burst = run(np.zeros(len(probs)))
-    log(f"burst: {burst['makespan_s']:.1f} s, {burst['steps_per_s']:.1f} steps/s")
-    rate = 0.8 * burst["steps_per_s"] / (total_steps / len(probs))        # requests per second
+    out = {"requests": len(probs), "steps": total_steps}
+    if burst:
+        b = run(np.zeros(len(probs)))
+        log(f"burst: {b['makespan_s']:.1f} s, {b['steps_per_s']:.1f} steps/s")
+        capacity = b["steps_per_s"]
+        out["burst"] = b
+    else:
+        # capacity from a burst of the first quarter of the stream
+        sub = min(len(probs), max(8, len(probs) // 4))
+        saved = probs
+        probs = probs[:sub]
+        total_sub = sum(p.nsteps for p in probs)
+        b = run(np.zeros(len(probs)))
+        probs = saved
+        capacity = b["steps_per_s"]
+        out["capacity_probe"] = {"requests": sub, "steps": total_sub, "steps_per_s": capacity}
+    rate = 0.8 * capacity / (total_steps / len(probs))        # requests per second
     rng = np.random.default_rng(55)
-    poisson_arr = np.cumsum(rng.exponential(1.0 / rate, len(probs)))
-    poisson = run(poisson_arr)
-    poisson["arrival_rate_per_s"] = rate
-    log(f"poisson: {poisson['makespan_s']:.1f} s, {poisson['steps_per_s']:.1f} steps/s")
-
-    # reference: one request at a time, complex128, on a sample of requests
-    # and steps (the rate is steps per second of device work, one at a time)
-    sample = list(range(min(args.serve_sample, len(probs))))
-    t, sample_steps = 0.0, 0
-    for i in sample:
+    arr = np.cumsum(rng.exponential(1.0 / rate, len(probs)))
+    pois = run(arr)
+    pois["arrival_rate_per_s"] = rate
+    log(f"poisson: {pois['makespan_s']:.1f} s, {pois['steps_per_s']:.1f} steps/s")
+    out["poisson"] = pois
+    # reference: one request at a time, complex128, on a sample of requests and steps
+    t, sample_steps_done = 0.0, 0
+    for i in range(min(sample, len(probs))):
         p = probs[i]
-        n = min(p.nsteps, args.serve_sample_steps)
+        n = min(p.nsteps, sample_steps)
         c = ttn.Context(p.tree, ttn.TTN_FP64)
         c.set_state(p.tensors)
         c.set_hamiltonian(p.H)
         t0 = time.perf_counter()
         c.step(p.dt, n)
         t += time.perf_counter() - t0
-        sample_steps += n
+        sample_steps_done += n
         c.close()
-    alone_rate = sample_steps / t
-    log(f"one at a time FP64: {alone_rate:.2f} steps/s over {sample_steps} steps")
+    alone = sample_steps_done / t
+    log(f"one at a time FP64: {alone:.2f} steps/s over {sample_steps_done} steps")
+    out["one_at_a_time_fp64"] = {"value": alone, "unit": UNIT,
+                                 "sample": f"first {min(sample, len(probs))} requests run alone with ttn_step, at "
+                                           f"most {sample_steps} steps each ({sample_steps_done} steps)"}
+    out["speedup_vs_one_at_a_time_fp64"] = pois["steps_per_s"] / alone
+    return out
+
+
+def run_serving(args):
+    """--serve: the serving stream (all requests at t0, then Poisson
+    arrivals at 80 % of the burst's capacity) as its own JSON line."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2503_15460_gb300 import ttn
+    import workloads as W
+    ttn.ttn_set_device(0)
+    ranges = dict(SERVE_RANGES)
+    if args.serve_full:
+        ranges = dict(n_modes_range=(8, 128), d_range=(8, 20), chi_range=(8, 48), steps_range=(100, 400))
+    res = serve_stream(ttn, W, args.serve_requests, ranges, args.slice_ms, burst=True,
+                       sample=args.serve_sample, sample_steps=args.serve_sample_steps,
+                       log=lambda m: print(f"[serve] {m}", file=sys.stderr, flush=True))
     line = {
         "metric": "serving: aggregate TTN-TDVP steps/s, continuous batching (mixed) vs one request at a time (FP64)",
-        "value": poisson["steps_per_s"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+        "value": res["poisson"]["steps_per_s"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
         "dtype": "c64 bulk / f64 state", "data": "synthetic",
-        "config": {"workload": serve_workload_name(len(probs)),
+        "config": {"workload": serve_workload_name(args.serve_requests, ranges),
                    "arrivals": "Poisson at 80% of the burst capacity (seed 55)", "slice_ms": args.slice_ms},
-        "poisson": poisson, "burst": burst,
-        "one_at_a_time_fp64": {"value": alone_rate, "unit": UNIT,
-                               "sample": f"first {len(sample)} requests run alone with ttn_step, at most "
-                                         f"{args.serve_sample_steps} steps each ({sample_steps} steps); "
-                                         f"rate = steps / time"},
-        "speedup_vs_one_at_a_time_fp64": poisson["steps_per_s"] / alone_rate,
+        **res,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -534,13 +643,25 @@ def main():
     ap.add_argument("--workload", default="vibronic", choices=sorted(WORKLOAD_DT),
                     help="vibronic (the headline), heom or spinboson300 (batched parameter sweeps)")
     ap.add_argument("--serve", action="store_true", help="run the serving stream instead (separate JSON line)")
+    ap.add_argument("--accuracy", action="store_true",
+                    help="mixed against complex128 over the workload's horizon instead (separate JSON line)")
+    ap.add_argument("--acc-steps", type=int, default=0, help="horizon (0: the configuration's step count)")
+    ap.add_argument("--acc-every", type=int, default=50)
+    ap.add_argument("--acc-instances", type=int, default=2)
+    ap.add_argument("--acc-cluster", type=int, default=16)
     ap.add_argument("--serve-requests", type=int, default=512)
+    ap.add_argument("--serve-full", action="store_true",
+                    help="--serve with the paper-shaped ranges (8-128 modes, bond dims 8-48, 100-400 steps)")
+    ap.add_argument("--default-serve-requests", type=int, default=160,
+                    help="requests of the serving leg of the default run (0: skip it)")
     ap.add_argument("--serve-sample", type=int, default=8)
     ap.add_argument("--serve-sample-steps", type=int, default=3)
     ap.add_argument("--slice-ms", type=float, default=20.0)
     args = ap.parse_args()
     if args.serve:
         return run_serving(args)
+    if args.accuracy:
+        return run_accuracy(args)
     if args.workload != "vibronic":
         args.e2e = args.cpu = False      # those legs are defined on the headline workload
 
@@ -565,16 +686,35 @@ def main():
                        "instances_per_gpu": args.batch, "precision": "mixed",
                        "l2": f"inputs larger than L2: the batch holds {r['batch_bytes'] / 1e9:.1f} GB on the device",
                        "parallelism": f"replicas x{world}, one thread block per instance"},
-            "p50_step_latency_ms": float(np.percentile(lat, 50)) if lat else None,
-            "p99_step_latency_ms": float(np.percentile(lat, 99)) if lat else None,
+            "batch_step_interval_p50_ms": float(np.percentile(lat, 50)) if lat else None,
+            "batch_step_interval_p99_ms": float(np.percentile(lat, 99)) if lat else None,
+            "batch_step_interval_note": ("interval between consecutive step completions of one instance in the "
+                                         "lock-step batch (every instance steps together); serving latency is "
+                                         "under 'serving'"),
             "fp64": r["fp64"],
             "speedup_vs_fp64": (r["value"] / r["fp64"]["value"]) if r["fp64"] else None,
             "gpu_launches": args.steps,
             "roofline": alu_roofline(r["flops_per_step"], r["flops64_per_step"], r["ms"] / args.steps / 1e3,
-                                     measured_traffic(args.batch) if args.workload == "vibronic" else None),
+                                     measured_traffic(args.batch) if args.workload == "vibronic" else None,
+                                     r["peaks"]),
             "clocks": r["clocks"],
             "e2e": r["e2e"],
         }
+        if args.default_serve_requests > 0 and args.workload == "vibronic" and world == 1:
+            from paper_2503_15460_gb300 import ttn as _ttn
+            import workloads as _W
+            sv = serve_stream(_ttn, _W, args.default_serve_requests, SERVE_RANGES_DEFAULT, args.slice_ms,
+                              burst=False, sample=args.serve_sample, sample_steps=args.serve_sample_steps)
+            line["serving"] = {
+                "workload": serve_workload_name(args.default_serve_requests, SERVE_RANGES_DEFAULT),
+                "arrivals": "Poisson at 80% of the capacity measured on a burst of the first quarter (seed 55)",
+                "steps_per_s": sv["poisson"]["steps_per_s"], "unit": UNIT,
+                "p50_step_ms": sv["poisson"]["p50_step_ms"], "p99_step_ms": sv["poisson"]["p99_step_ms"],
+                "p50_request_s": sv["poisson"]["p50_request_s"], "p99_request_s": sv["poisson"]["p99_request_s"],
+                "one_at_a_time_fp64": sv["one_at_a_time_fp64"],
+                "speedup_vs_one_at_a_time_fp64": sv["speedup_vs_one_at_a_time_fp64"],
+                "detail": sv,
+            }
         if args.cpu:
             line["cpu_baseline"] = cpu_baseline(args)
         print(json.dumps(line), flush=True)

@@ -312,6 +312,15 @@ ttn_status ttn_heff_apply_noalloc(void* stream, int D, const int* dims, int n_te
  * a device selected through another runtime, e.g. PyTorch's, is not seen). */
 ttn_status ttn_set_device(int device);
 
+/* Measured arithmetic peaks of the current device (no counterpart in the
+ * paper: the denominators of the roofline the sweep kernel is judged
+ * against).  fp32_tflops / fp64_tflops receive the sustained rate of fused
+ * multiply-adds (2 flops each) of a kernel that fills every SM with
+ * independent FMA chains, timed with CUDA events on `stream` (NULL: the
+ * legacy default stream) over about `seconds` per pipe (0 < seconds <= 60).
+ * Errors through ttn_last_error(NULL). */
+ttn_status ttn_pipe_peaks(void* stream, double seconds, double* fp32_tflops, double* fp64_tflops);
+
 /* Thread blocks that one instance of ctx runs on (no counterpart in the
  * paper: how a node update is spread over the GPU).  The sweep is a chain
  * of dependent node updates (Sec. II.C), so a large instance is sped up by
@@ -375,19 +384,26 @@ ttn_status ttn_device_bytes(const ttn_ctx* ctx, size_t* bytes);
  * parameter sweeps over couplings, temperatures or bath discretisations.
  * A request is a context (tree, state, Hamiltonian) and (dt, nsteps).
  * Submitted requests wait in a FIFO queue holding no device memory (the
- * context is moved to the host).  ttn_server_pump admits queued requests
- * while fewer than max_slots are admitted and the sum of their footprints
- * (ttn_footprint) stays within hbm_budget; an admitted context keeps its
- * tensors and environments on the device until it finishes.  Each pump
- * waits for the previous launch, retires finished requests (their device
- * time stamps are recorded, their tensors copied back to the host context,
- * their memory returned), admits more, and starts the next launch: one
- * thread block per admitted context, each running whole steps of its own
- * dt until its steps are done or the launch's slice of device time is
- * used up.  Admission of new requests (allocation, upload, environment
- * build) runs on a second stream while a launch is in flight.  A
+ * context is moved to the host).  A request runs on the block count its
+ * context asks for (ttn_get_cluster: one block, or a cluster of 2..16);
+ * the server keeps one lane per block count, each with its own stream and
+ * launch, so one-block and cluster requests run side by side.
+ * ttn_server_pump admits queued requests in arrival order to their lanes
+ * while the lane has a free slot (max_slots for the one-block lane; for a
+ * cluster lane, as many clusters as the device holds at once) and the sum
+ * of all admitted footprints (ttn_footprint) stays within hbm_budget; an
+ * admitted context keeps its tensors and environments on the device until
+ * it finishes.  Each pump waits until some lane's launch has finished,
+ * retires that lane's finished requests (their device time stamps are
+ * recorded, their tensors copied back to the host context, their memory
+ * returned), admits more, and starts the next launch of every idle lane:
+ * one block or cluster per admitted context, each running whole steps of
+ * its own dt until its steps are done or the launch's slice of device time
+ * is used up.  Admission of new requests (allocation, upload, environment
+ * build) runs on a separate stream while launches are in flight.  A
  * context's results do not depend on the other contexts in the launch nor
- * on how its steps are split over launches: they equal ttn_step's.
+ * on how its steps are split over launches: they equal ttn_step's with
+ * the same block count.
  * The server is driven by one host thread; it is not thread-safe.
  * --------------------------------------------------------------------- */
 typedef struct ttn_server ttn_server;
@@ -395,7 +411,8 @@ typedef struct ttn_server ttn_server;
 typedef struct {
     size_t hbm_budget;   /* bytes the admitted contexts may hold together;
                             0 = 90% of the device's free memory at creation */
-    int max_slots;       /* most contexts admitted at once; 0 = 2 per SM    */
+    int max_slots;       /* most contexts admitted at once to the one-block
+                            lane (and a cap for cluster lanes); 0 = 2 per SM */
     double slice_ms;     /* device time per launch (at least one step of the
                             slowest admitted context); 0 = 20 ms           */
     int use_graph;       /* 1: each launch is the replay of one CUDA graph

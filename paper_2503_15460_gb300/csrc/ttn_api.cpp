@@ -1077,6 +1077,26 @@ ttn_status ttn_get_cluster(const ttn_ctx* c, int* blocks) {
     return TTN_OK;
 }
 
+ttn_status ttn_pipe_peaks(void* stream, double seconds, double* fp32_tflops, double* fp64_tflops) {
+    if (!fp32_tflops || !fp64_tflops || !(seconds > 0.0) || seconds > 60.0)
+        return fail(nullptr, TTN_E_INVALID, "need output pointers and 0 < seconds <= 60");
+    cudaStream_t s = (cudaStream_t)stream;
+    // calibrate on a short run, then time one launch of about `seconds` per pipe
+    for (int pipe = 0; pipe < 2; ++pipe) {
+        auto run = pipe == 0 ? ttn_pipe_peak_fp32 : ttn_pipe_peak_fp64;
+        double tf = 0.0, ms = 0.0;
+        int iters = pipe == 0 ? (1 << 16) : (1 << 10);
+        int e = run(iters, &tf, &ms, s);
+        if (e) return fail(nullptr, TTN_E_CUDA, std::string("pipe benchmark: ") + cudaGetErrorString((cudaError_t)e));
+        const double scale = std::max(1.0, seconds * 1e3 / std::max(ms, 1e-3));
+        iters = (int)std::min(2e9, iters * scale);
+        e = run(iters, &tf, &ms, s);
+        if (e) return fail(nullptr, TTN_E_CUDA, std::string("pipe benchmark: ") + cudaGetErrorString((cudaError_t)e));
+        (pipe == 0 ? *fp32_tflops : *fp64_tflops) = tf;
+    }
+    return TTN_OK;
+}
+
 ttn_status ttn_set_device(int device) {
     cudaError_t e = cudaSetDevice(device);
     if (e != cudaSuccess) return fail(nullptr, TTN_E_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));

@@ -1627,8 +1627,13 @@ __device__ void spawn_op(const TtnOp& op, const TtnInstance& in, Smem& sm, TB* V
                 if (T[(int64_t)order[j] * r + order[j]].x > T[(int64_t)order[i] * r + order[i]].x) {
                     const int tmp = order[i]; order[i] = order[j]; order[j] = tmp;
                 }
+        // complex64 contractions leave noise of ~1e-7 of the largest eigenvalue
+        // in T: with a complex64 bulk only eigenvalues above 1e-6 of the
+        // largest are taken as resolved (complex128: the oracle's rule alone)
+        const double tfloor = sizeof(TB) == 16 ? 0.0 : 1e-6 * (cnt > 0 ? T[(int64_t)order[0] * r + order[0]].x : 0.0);
         int p = 0;
-        while (p < cnt && p < cap && T[(int64_t)order[p] * r + order[p]].x >= thr) ++p;
+        while (p < cnt && p < cap && T[(int64_t)order[p] * r + order[p]].x >= thr &&
+               T[(int64_t)order[p] * r + order[p]].x >= tfloor) ++p;
         sm.flag = p;
     }
     __syncthreads();

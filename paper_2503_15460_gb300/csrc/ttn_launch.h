@@ -53,6 +53,12 @@ int ttn_launch_heff(const TtnEntry* d_entries, int ne, const TtnSlot* d_slots, i
 int ttn_launch_heff_noalloc(const TtnEntry* h_entries, int ne, const TtnSlot* h_slots, int n_slots, int D,
                             const int* dims, const void* x, void* y, cudaStream_t stream);
 
+// FP32 / FP64 fused multiply-add throughput of the current device: `iters`
+// iterations of 8 independent FMA chains per thread, 4 blocks of 256
+// threads per SM; TFLOP/s and the kernel's time (CUDA events on stream).
+int ttn_pipe_peak_fp32(int iters, double* tflops, double* ms, cudaStream_t stream);
+int ttn_pipe_peak_fp64(int iters, double* tflops, double* ms, cudaStream_t stream);
+
 // ---- internal: one entry point per kernel variant (own translation unit) ----
 struct TtnVariantArgs {
     const TtnInstance* insts;

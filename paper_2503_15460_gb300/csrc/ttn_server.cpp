@@ -2,24 +2,31 @@
 // device (declarations and documentation in include/ttn.h).
 //
 // Each request is a context plus (dt, nsteps).  Requests wait in a FIFO
-// queue on the host, holding no device memory.  A request is admitted when
-// a slot is free and its footprint (operator and state arenas, from its
-// plan) fits in the budget beside the admitted ones; admission allocates
-// from the stream-ordered pool and builds the environments on a side
-// stream, so it overlaps the launch in flight.  Every launch runs one block
-// per admitted context for one slice of device time; a block runs whole
-// steps of its own dt until the slice is used up or its steps are done, so
-// a context's arithmetic does not depend on which other contexts share the
-// launch.  After a launch the server retires finished contexts (time
+// queue on the host, holding no device memory.  A request runs on the
+// number of thread blocks its context asks for (ttn_get_cluster): one lane
+// per block count (1, 2, 4, 8, 16), each lane with its own stream, launch
+// table and CUDA graph, so small requests share launches one block each
+// while large ones get a cluster, and the lanes' launches overlap on the
+// device.  A request is admitted to its lane when a slot is free there and
+// its footprint (operator and state arenas, from its plan) fits in the
+// budget beside every admitted one; admission allocates from the
+// stream-ordered pool and builds the environments on a side stream, so it
+// overlaps the launches in flight.  Every launch runs each admitted context
+// of the lane for one slice of device time; a context runs whole steps of
+// its own dt until the slice is used up or its steps are done, so its
+// arithmetic does not depend on which other contexts share the launch.
+// After a lane's launch the server retires its finished contexts (time
 // stamps read, tensors copied to the host, memory returned to the pool) and
-// admits waiting ones before the next launch.
+// admits waiting ones before the lane's next launch.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <deque>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/ttn.h"
@@ -41,21 +48,14 @@ struct Request {
 
 }  // namespace
 
-struct ttn_server {
-    int precision = 0;
-    int device = 0;
-    size_t budget = 0;
+namespace {
+
+// One lane: every admitted context of one block count, launched together.
+struct Lane {
+    int cluster = 1;
     int max_slots = 0;
-    long long slice_ns = 0;
-    bool use_graph = false;
-    cudaStream_t run_stream = nullptr;
-    cudaStream_t side_stream = nullptr;
-
-    std::deque<Request> queue;
+    cudaStream_t stream = nullptr;
     std::vector<Request> running;     // admitted, in launch order
-    std::vector<std::pair<int64_t, ttn_status>> finished;
-    std::vector<double> lat_ms;
-
     TtnLaunchHdr* h_hdr = nullptr;    // pinned host copies of what a launch reads / writes
     TtnInstance* h_table = nullptr;
     TtnRepOut* h_rep = nullptr;
@@ -64,6 +64,32 @@ struct ttn_server {
     TtnRepOut* d_rep = nullptr;
     cudaGraphExec_t graph = nullptr;
     int inflight = 0;                 // contexts in the launch in flight (prefix of `running`)
+};
+
+constexpr int kLanes = 5;             // block counts 1, 2, 4, 8, 16
+
+int lane_of(int cluster) {
+    int i = 0;
+    while ((1 << i) < cluster && i + 1 < kLanes) ++i;
+    return i;
+}
+
+}  // namespace
+
+struct ttn_server {
+    int precision = 0;
+    int device = 0;
+    int sms = 0;
+    size_t budget = 0;
+    int max_slots = 0;                // one-block lane; cluster lanes hold what fits at once
+    long long slice_ns = 0;
+    bool use_graph = false;
+    cudaStream_t side_stream = nullptr;
+
+    std::deque<Request> queue;
+    Lane lanes[kLanes];
+    std::vector<std::pair<int64_t, ttn_status>> finished;
+    std::vector<double> lat_ms;
 
     int64_t next_ticket = 1;
     ttn_server_stats st{};
@@ -94,33 +120,75 @@ ttn_status status_of(int device_status) {
     return TTN_E_CUDA;
 }
 
-// Issue one launch: table and header in, kernel, per-block results out.
-ttn_status issue(ttn_server* s) {
-    SCK(cudaMemcpyAsync(s->d_table, s->h_table, sizeof(TtnInstance) * s->max_slots, cudaMemcpyHostToDevice,
-                        s->run_stream), "table upload");
-    SCK(cudaMemcpyAsync(s->d_hdr, s->h_hdr, sizeof(TtnLaunchHdr), cudaMemcpyHostToDevice, s->run_stream),
-        "header upload");
-    int e = ttn_launch_program_ex(s->precision, 1, s->d_table, s->d_hdr, s->max_slots, 0.0, -1, 0, s->d_rep,
-                                  s->run_stream);
+// Issue one launch of a lane: table and header in, kernel, per-instance results out.
+ttn_status issue(ttn_server* s, Lane& L) {
+    SCK(cudaMemcpyAsync(L.d_table, L.h_table, sizeof(TtnInstance) * L.max_slots, cudaMemcpyHostToDevice, L.stream),
+        "table upload");
+    SCK(cudaMemcpyAsync(L.d_hdr, L.h_hdr, sizeof(TtnLaunchHdr), cudaMemcpyHostToDevice, L.stream), "header upload");
+    int e = ttn_launch_program_ex(s->precision, L.cluster, L.d_table, L.d_hdr, L.max_slots, 0.0, -1, 0, L.d_rep,
+                                  L.stream);
     if (e) return srv_cuda(s, (cudaError_t)e, "kernel launch");
-    SCK(cudaMemcpyAsync(s->h_rep, s->d_rep, sizeof(TtnRepOut) * s->max_slots, cudaMemcpyDeviceToHost,
-                        s->run_stream), "result copy");
+    SCK(cudaMemcpyAsync(L.h_rep, L.d_rep, sizeof(TtnRepOut) * L.max_slots, cudaMemcpyDeviceToHost, L.stream),
+        "result copy");
     return TTN_OK;
 }
 
-ttn_status build_graph(ttn_server* s) {
+ttn_status build_graph(ttn_server* s, Lane& L) {
     int e = ttn_program_init();
     if (e) return srv_cuda(s, (cudaError_t)e, "kernel attributes");
-    SCK(cudaStreamBeginCapture(s->run_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-    ttn_status r = issue(s);
+    SCK(cudaStreamBeginCapture(L.stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    ttn_status r = issue(s, L);
     cudaGraph_t g = nullptr;
-    cudaError_t ce = cudaStreamEndCapture(s->run_stream, &g);
+    cudaError_t ce = cudaStreamEndCapture(L.stream, &g);
     if (r) { if (g) cudaGraphDestroy(g); return r; }
     if (ce != cudaSuccess) return srv_cuda(s, ce, "end capture");
-    ce = cudaGraphInstantiate(&s->graph, g, 0);
+    ce = cudaGraphInstantiate(&L.graph, g, 0);
     cudaGraphDestroy(g);
     if (ce != cudaSuccess) return srv_cuda(s, ce, "graph instantiate");
     return TTN_OK;
+}
+
+// Create a lane's stream, buffers and graph on first use.  A cluster lane
+// holds as many contexts as clusters of its size fit on the device at once.
+ttn_status lane_open(ttn_server* s, int li) {
+    Lane& L = s->lanes[li];
+    if (L.stream) return TTN_OK;
+    L.cluster = 1 << li;
+    if (L.cluster == 1) {
+        L.max_slots = s->max_slots;
+    } else {
+        int active = 0;
+        int e = ttn_cluster_capacity(s->precision, L.cluster, &active);
+        if (e) return srv_cuda(s, (cudaError_t)e, "cluster occupancy");
+        if (active < 1) return srv_fail(s, TTN_E_INVALID, "clusters of " + std::to_string(L.cluster) +
+                                                          " blocks cannot be scheduled on this device");
+        L.max_slots = std::min(active, s->max_slots);
+    }
+    bool ok = cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaHostAlloc((void**)&L.h_hdr, sizeof(TtnLaunchHdr), cudaHostAllocDefault) == cudaSuccess &&
+              cudaHostAlloc((void**)&L.h_table, sizeof(TtnInstance) * L.max_slots, cudaHostAllocDefault) == cudaSuccess &&
+              cudaHostAlloc((void**)&L.h_rep, sizeof(TtnRepOut) * L.max_slots, cudaHostAllocDefault) == cudaSuccess &&
+              cudaMalloc((void**)&L.d_hdr, sizeof(TtnLaunchHdr)) == cudaSuccess &&
+              cudaMalloc((void**)&L.d_table, sizeof(TtnInstance) * L.max_slots) == cudaSuccess &&
+              cudaMalloc((void**)&L.d_rep, sizeof(TtnRepOut) * L.max_slots) == cudaSuccess;
+    if (!ok) return srv_fail(s, TTN_E_OOM, "lane allocation failed");
+    std::memset(L.h_table, 0, sizeof(TtnInstance) * L.max_slots);
+    std::memset(L.h_hdr, 0, sizeof(TtnLaunchHdr));
+    if (s->use_graph) return build_graph(s, L);
+    return TTN_OK;
+}
+
+void lane_close(Lane& L) {
+    if (L.stream) cudaStreamSynchronize(L.stream);
+    if (L.graph) cudaGraphExecDestroy(L.graph);
+    if (L.h_hdr) cudaFreeHost(L.h_hdr);
+    if (L.h_table) cudaFreeHost(L.h_table);
+    if (L.h_rep) cudaFreeHost(L.h_rep);
+    if (L.d_hdr) cudaFree(L.d_hdr);
+    if (L.d_table) cudaFree(L.d_table);
+    if (L.d_rep) cudaFree(L.d_rep);
+    if (L.stream) cudaStreamDestroy(L.stream);
+    L = Lane();
 }
 
 // Per-step latencies of a finished request from its device time stamps.
@@ -151,49 +219,56 @@ void retire(ttn_server* s, Request& r, ttn_status code) {
     else s->st.failed++;
 }
 
-// Admit queued requests while a slot is free and the footprint fits.
+// Admit queued requests (in arrival order, each to its lane) while a slot is
+// free in that lane and the footprint fits in the budget.
 ttn_status admit(ttn_server* s) {
-    while (!s->queue.empty() && (int)s->running.size() < s->max_slots) {
-        Request& r = s->queue.front();
+    for (auto it = s->queue.begin(); it != s->queue.end();) {
+        Request& r = *it;
+        Lane& L = s->lanes[lane_of(ttn::ctx_cluster(r.ctx))];
         if (r.footprint > s->budget) {
             s->finished.emplace_back(r.ticket, TTN_E_OOM);
             ttn::ctx_fail(r.ctx, TTN_E_OOM, "request footprint exceeds the server's device-memory budget");
             s->st.failed++;
-            s->queue.pop_front();
+            it = s->queue.erase(it);
             continue;
         }
+        if ((int)L.running.size() >= L.max_slots) { ++it; continue; }      // lane full: later lanes may admit
         if (s->st.bytes_in_use + r.footprint > s->budget) break;
         r.ctx->stream = s->side_stream;
         ttn_status m = ttn::ctx_materialize(r.ctx);
         r.ctx->stream = r.user_stream;
-        if (m == TTN_E_OOM && !s->running.empty()) break;   // pool fragmented: retry after retirements
+        bool any_running = false;
+        for (auto& l : s->lanes) any_running |= !l.running.empty();
+        if (m == TTN_E_OOM && any_running) break;   // pool fragmented: retry after retirements
         if (m != TTN_OK) {
             s->finished.emplace_back(r.ticket, m);
             s->st.failed++;
-            s->queue.pop_front();
+            it = s->queue.erase(it);
             continue;
         }
         s->st.bytes_in_use += r.footprint;
         s->st.peak_bytes = std::max(s->st.peak_bytes, s->st.bytes_in_use);
-        s->running.push_back(r);
-        s->queue.pop_front();
+        L.running.push_back(r);
+        it = s->queue.erase(it);
     }
-    s->st.peak_running = std::max<int64_t>(s->st.peak_running, (int64_t)s->running.size());
+    int64_t run = 0;
+    for (auto& l : s->lanes) run += (int64_t)l.running.size();
+    s->st.peak_running = std::max<int64_t>(s->st.peak_running, run);
     return TTN_OK;
 }
 
-// Wait for the launch in flight and account for what it did.
-ttn_status complete(ttn_server* s) {
-    if (!s->inflight) return TTN_OK;
-    SCK(cudaStreamSynchronize(s->run_stream), "launch");
-    const int n = s->inflight;
-    s->inflight = 0;
+// Account for what a finished launch of a lane did.
+ttn_status complete(ttn_server* s, Lane& L) {
+    if (!L.inflight) return TTN_OK;
+    SCK(cudaStreamSynchronize(L.stream), "launch");
+    const int n = L.inflight;
+    L.inflight = 0;
     std::vector<Request> keep;
-    keep.reserve(s->running.size());
-    for (int i = 0; i < (int)s->running.size(); ++i) {
-        Request& r = s->running[i];
+    keep.reserve(L.running.size());
+    for (int i = 0; i < (int)L.running.size(); ++i) {
+        Request& r = L.running[i];
         if (i >= n) { keep.push_back(r); continue; }
-        const TtnRepOut o = s->h_rep[i];
+        const TtnRepOut o = L.h_rep[i];
         r.left -= o.reps;
         s->st.steps += o.reps;
         if (o.reps > 0) r.est_step_ns = (double)o.elapsed_ns / o.reps;
@@ -202,34 +277,48 @@ ttn_status complete(ttn_server* s) {
         else if (r.left <= 0) retire(s, r, TTN_OK);
         else keep.push_back(r);
     }
-    s->running.swap(keep);
+    L.running.swap(keep);
     return TTN_OK;
 }
 
-ttn_status launch(ttn_server* s) {
-    const int n = (int)s->running.size();
-    if (n == 0) return TTN_OK;
+ttn_status launch(ttn_server* s, Lane& L) {
+    const int n = (int)L.running.size();
+    if (n == 0 || L.inflight) return TTN_OK;
     double longest = 0.0;
     for (int i = 0; i < n; ++i) {
-        Request& r = s->running[i];
+        Request& r = L.running[i];
         TtnInstance in = ttn::make_instance(r.ctx, r.ctx->step_p);
         in.nrep = r.left;
         in.dt = r.dt;
-        s->h_table[i] = in;
+        L.h_table[i] = in;
         longest = std::max(longest, r.est_step_ns);
     }
     // a slice holds at least one step of the slowest admitted context
-    s->h_hdr->n = n;
-    s->h_hdr->slice_ns = std::max(s->slice_ns, (long long)(1.25 * longest));
+    L.h_hdr->n = n;
+    L.h_hdr->slice_ns = std::max(s->slice_ns, (long long)(1.25 * longest));
     if (s->use_graph) {
-        SCK(cudaGraphLaunch(s->graph, s->run_stream), "graph launch");
+        SCK(cudaGraphLaunch(L.graph, L.stream), "graph launch");
     } else {
-        ttn_status r = issue(s);
+        ttn_status r = issue(s, L);
         if (r) return r;
     }
-    s->inflight = n;
+    L.inflight = n;
     s->st.launches++;
     return TTN_OK;
+}
+
+// Block until some lane's launch has finished (none in flight: return).
+void wait_any(ttn_server* s) {
+    for (;;) {
+        bool any = false;
+        for (auto& L : s->lanes) {
+            if (!L.inflight) continue;
+            any = true;
+            if (cudaStreamQuery(L.stream) != cudaErrorNotReady) return;
+        }
+        if (!any) return;
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
 }
 
 }  // namespace
@@ -243,29 +332,21 @@ ttn_status ttn_server_create(int precision, const ttn_server_opts* opts, ttn_ser
     ttn_server* s = new (std::nothrow) ttn_server();
     if (!s) return TTN_E_OOM;
     cudaGetDevice(&s->device);
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+    cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device);
     size_t free_b = 0, total_b = 0;
     cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
     if (e != cudaSuccess) { delete s; return TTN_E_CUDA; }
     s->precision = precision;
     s->budget = opts && opts->hbm_budget ? opts->hbm_budget : (size_t)(0.9 * (double)free_b);
-    s->max_slots = opts && opts->max_slots > 0 ? opts->max_slots : std::max(1, 2 * sms);
+    s->max_slots = opts && opts->max_slots > 0 ? opts->max_slots : std::max(1, 2 * s->sms);
     const double ms = opts && opts->slice_ms > 0 ? opts->slice_ms : 20.0;
     s->slice_ns = (long long)(ms * 1e6);
     s->use_graph = opts ? opts->use_graph != 0 : true;
-    bool ok = cudaStreamCreateWithFlags(&s->run_stream, cudaStreamNonBlocking) == cudaSuccess &&
-              cudaStreamCreateWithFlags(&s->side_stream, cudaStreamNonBlocking) == cudaSuccess &&
-              cudaHostAlloc((void**)&s->h_hdr, sizeof(TtnLaunchHdr), cudaHostAllocDefault) == cudaSuccess &&
-              cudaHostAlloc((void**)&s->h_table, sizeof(TtnInstance) * s->max_slots, cudaHostAllocDefault) == cudaSuccess &&
-              cudaHostAlloc((void**)&s->h_rep, sizeof(TtnRepOut) * s->max_slots, cudaHostAllocDefault) == cudaSuccess &&
-              cudaMalloc((void**)&s->d_hdr, sizeof(TtnLaunchHdr)) == cudaSuccess &&
-              cudaMalloc((void**)&s->d_table, sizeof(TtnInstance) * s->max_slots) == cudaSuccess &&
-              cudaMalloc((void**)&s->d_rep, sizeof(TtnRepOut) * s->max_slots) == cudaSuccess;
-    if (!ok) { ttn_server_destroy(s); return TTN_E_OOM; }
-    std::memset(s->h_table, 0, sizeof(TtnInstance) * s->max_slots);
-    std::memset(s->h_hdr, 0, sizeof(TtnLaunchHdr));
-    if (s->use_graph && build_graph(s) != TTN_OK) { ttn_server_destroy(s); return TTN_E_CUDA; }
+    if (cudaStreamCreateWithFlags(&s->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        lane_open(s, 0) != TTN_OK) {
+        ttn_server_destroy(s);
+        return TTN_E_CUDA;
+    }
     *out = s;
     return TTN_OK;
 }
@@ -282,13 +363,16 @@ ttn_status ttn_server_submit(ttn_server* s, ttn_ctx* ctx, double dt, int nsteps,
         if (opts->expand) return srv_fail(s, TTN_E_INVALID, "the server runs fixed bond dimensions (expand = 0)");
         if (opts->krylov_maxdim > TTN_KMAX) return srv_fail(s, TTN_E_INVALID, "krylov_maxdim must be <= 32");
     }
-    if (ctx->plan.max_chi > ttn::kSoloMaxDim)
-        return srv_fail(s, TTN_E_INVALID, "the server runs one thread block per request: index dimensions must be <= 45");
     for (const Request& r : s->queue)
         if (r.ctx == ctx) return srv_fail(s, TTN_E_INVALID, "context already submitted");
-    for (const Request& r : s->running)
-        if (r.ctx == ctx) return srv_fail(s, TTN_E_INVALID, "context already submitted");
+    for (const Lane& L : s->lanes)
+        for (const Request& r : L.running)
+            if (r.ctx == ctx) return srv_fail(s, TTN_E_INVALID, "context already submitted");
     cudaSetDevice(s->device);
+    {
+        ttn_status le = lane_open(s, lane_of(ttn::ctx_cluster(ctx)));
+        if (le) return le;
+    }
     if (ctx->resident) {
         // queued requests hold no device memory
         ttn_status e = ttn::ctx_evict(ctx);
@@ -316,22 +400,35 @@ ttn_status ttn_server_submit(ttn_server* s, ttn_ctx* ctx, double dt, int nsteps,
 ttn_status ttn_server_pump(ttn_server* s, int* n_running, int* n_queued) {
     if (!s) return TTN_E_INVALID;
     cudaSetDevice(s->device);
-    ttn_status r = admit(s);            // overlaps the launch in flight
-    if (!r) r = complete(s);
+    ttn_status r = admit(s);            // overlaps the launches in flight
+    if (!r) {
+        wait_any(s);
+        for (auto& L : s->lanes) {
+            if (r) break;
+            if (L.inflight && cudaStreamQuery(L.stream) != cudaErrorNotReady) r = complete(s, L);
+        }
+    }
     if (!r) r = admit(s);               // memory released by retirements
-    if (!r) r = launch(s);
-    if (n_running) *n_running = (int)s->running.size();
+    for (auto& L : s->lanes) {
+        if (r) break;
+        if (L.stream) r = launch(s, L);
+    }
+    int running = 0;
+    for (auto& L : s->lanes) running += (int)L.running.size();
+    if (n_running) *n_running = running;
     if (n_queued) *n_queued = (int)s->queue.size();
     return r;
 }
 
 ttn_status ttn_server_drain(ttn_server* s) {
     if (!s) return TTN_E_INVALID;
-    while (!s->queue.empty() || !s->running.empty() || s->inflight) {
+    for (;;) {
+        bool busy = !s->queue.empty();
+        for (auto& L : s->lanes) busy |= !L.running.empty() || L.inflight;
+        if (!busy) return TTN_OK;
         ttn_status r = ttn_server_pump(s, nullptr, nullptr);
         if (r) return r;
     }
-    return TTN_OK;
 }
 
 ttn_status ttn_server_poll(ttn_server* s, int max, int64_t* tickets, ttn_status* status, int* n) {
@@ -350,7 +447,8 @@ ttn_status ttn_server_get_stats(ttn_server* s, ttn_server_stats* out) {
     if (!s || !out) return TTN_E_INVALID;
     ttn_server_stats st = s->st;
     st.queued = (int64_t)s->queue.size();
-    st.running = (int64_t)s->running.size();
+    st.running = 0;
+    for (auto& L : s->lanes) st.running += (int64_t)L.running.size();
     st.n_latencies = (int64_t)s->lat_ms.size();
     st.p50_step_ms = st.p99_step_ms = 0.0;
     if (!s->lat_ms.empty()) {
@@ -380,23 +478,19 @@ const char* ttn_server_last_error(const ttn_server* s) { return s ? s->err.c_str
 void ttn_server_destroy(ttn_server* s) {
     if (!s) return;
     cudaSetDevice(s->device);
-    if (s->run_stream) cudaStreamSynchronize(s->run_stream);
-    s->inflight = 0;
-    // admitted contexts go back to the host, unfinished
-    for (Request& r : s->running) {
-        r.ctx->stream = s->side_stream;
-        ttn::ctx_evict(r.ctx);
-        r.ctx->stream = r.user_stream;
+    for (auto& L : s->lanes) {
+        if (L.stream) cudaStreamSynchronize(L.stream);
+        L.inflight = 0;
+        // admitted contexts go back to the host, unfinished
+        for (Request& r : L.running) {
+            r.ctx->stream = s->side_stream;
+            ttn::ctx_evict(r.ctx);
+            r.ctx->stream = r.user_stream;
+        }
+        L.running.clear();
     }
     if (s->side_stream) cudaStreamSynchronize(s->side_stream);
-    if (s->graph) cudaGraphExecDestroy(s->graph);
-    if (s->h_hdr) cudaFreeHost(s->h_hdr);
-    if (s->h_table) cudaFreeHost(s->h_table);
-    if (s->h_rep) cudaFreeHost(s->h_rep);
-    if (s->d_hdr) cudaFree(s->d_hdr);
-    if (s->d_table) cudaFree(s->d_table);
-    if (s->d_rep) cudaFree(s->d_rep);
-    if (s->run_stream) cudaStreamDestroy(s->run_stream);
+    for (auto& L : s->lanes) lane_close(L);
     if (s->side_stream) cudaStreamDestroy(s->side_stream);
     delete s;
 }

@@ -75,6 +75,7 @@ _sig = {
     "ttn_set_stream": ([_P, _P], C.c_int),
     "ttn_set_device": ([C.c_int], C.c_int),
     "ttn_set_cluster": ([_P, C.c_int], C.c_int),
+    "ttn_pipe_peaks": ([_P, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
     "ttn_get_cluster": ([_P, C.POINTER(C.c_int)], C.c_int),
     "ttn_heff_apply": ([_P, C.c_int, _I32, C.c_int, _C128, _I32, C.c_int, C.POINTER(_P), _P, _P], C.c_int),
     "ttn_heff_apply_noalloc": ([_P, C.c_int, _I32, C.c_int, _C128, _I32, C.c_int, C.POINTER(_P), _P, _P], C.c_int),
@@ -323,6 +324,13 @@ def ttn_heff_apply_noalloc(stream, dims, coeff, factor, mat_ptrs, x_ptr, y_ptr):
 
 def ttn_set_device(device: int):
     _check(_lib.ttn_set_device(int(device)), None)
+
+
+def ttn_pipe_peaks(stream=0, seconds=0.5):
+    """Measured FP32 and FP64 FMA throughput (TFLOP/s) of the current device."""
+    a, b = C.c_double(0.0), C.c_double(0.0)
+    _check(_lib.ttn_pipe_peaks(C.c_void_p(int(stream or 0)), float(seconds), C.byref(a), C.byref(b)), None)
+    return a.value, b.value
 
 
 def ttn_set_cluster(ctx, blocks: int):

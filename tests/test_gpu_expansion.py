@@ -137,7 +137,12 @@ def test_expansion_growth_above_16_fp64(gpu_lib, many_channel_floor):
     assert worst <= max(1e-10, 20.0 * many_channel_floor)
 
 
-def test_expansion_growth_above_16_mixed(gpu_lib, many_channel_floor):
-    jump, worst = _largest_growth(gpu_lib, many_channel_problem(), 3, 1e-6, 32, gpu_lib.TTN_MIXED)
+def test_expansion_growth_above_16_mixed(gpu_lib):
+    """Complex64 contractions resolve eigenvalues of the spawning operator
+    down to about 1e-6 of the largest; at eps 3e-5 the growth of 17 functions
+    has its smallest accepted eigenvalue at 3.2e-6 of the largest and its
+    first rejected one 8 % below the threshold in sigma, so the decisions
+    are clear of both the threshold and the complex64 floor."""
+    jump, worst = _largest_growth(gpu_lib, many_channel_problem(), 3, 3e-5, 32, gpu_lib.TTN_MIXED)
     assert jump > 16
-    assert worst <= max(1e-6, 20.0 * many_channel_floor)
+    assert worst <= 1e-6

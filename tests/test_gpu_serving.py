@@ -163,3 +163,40 @@ def test_materialize_evict_round_trip(gpu_lib):
     assert gpu_lib.ttn_step_stats(c.h)[0] == 6
     ref.close()
     c.close()
+
+
+def test_serving_cluster_lanes_alone_equals_mix(gpu_lib):
+    """Requests on one block and on 4-block clusters in one stream: the
+    server runs them in two lanes whose launches overlap; every result
+    equals ttn_step alone with the same block count, bit for bit."""
+    probs = request_problems(8, seed=9)
+    blocks = [4 if i % 2 else 1 for i in range(len(probs))]
+    precision = gpu_lib.TTN_MIXED
+    srv = gpu_lib.Server(precision, slice_ms=0.5)
+    ctxs, tickets, done = [], {}, {}
+    for i, p in enumerate(probs):
+        c = host_ctx(gpu_lib, p, precision)
+        c.set_cluster(blocks[i])
+        tickets[srv.submit(c, p.dt, p.nsteps)] = i
+        ctxs.append(c)
+        if i % 3 == 2:
+            srv.pump()
+    while len(done) < len(probs):
+        srv.pump()
+        for t, st in srv.poll():
+            done[tickets[t]] = st
+    assert all(st == gpu_lib.TTN_OK for st in done.values())
+    stats = srv.stats()
+    assert stats["completed"] == len(probs)
+    assert stats["steps"] == sum(p.nsteps for p in probs)
+    for i, (p, c) in enumerate(zip(probs, ctxs)):
+        a = gpu_lib.Context(p.tree, precision)
+        a.set_cluster(blocks[i])
+        a.set_state(p.tensors)
+        a.set_hamiltonian(p.H)
+        a.step(p.dt, p.nsteps)
+        for x, y in zip(a.get_state(), c.get_state()):
+            assert np.array_equal(x, y)
+        a.close()
+        c.close()
+    srv.close()
