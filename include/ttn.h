@@ -312,6 +312,55 @@ ttn_status ttn_heff_apply_noalloc(void* stream, int D, const int* dims, int n_te
  * a device selected through another runtime, e.g. PyTorch's, is not seen). */
 ttn_status ttn_set_device(int device);
 
+/* Autotuning (no counterpart in the paper): pick the launch shape and the
+ * contraction routines for ctx's own problem by timing them on the device.
+ * Every trial restores a snapshot of everything a step modifies (node
+ * tensors, bond buffer, Krylov workspace, counters, environment and
+ * channel matrices), runs `steps` steps of length dt and times them with
+ * CUDA events on the context's stream; the fastest configuration is kept
+ * and the context is left exactly as it was before the call (the same
+ * bits).  flags (bitwise or):
+ *   1  thread blocks per instance (1, 2, 4, 8, 16; see ttn_set_cluster);
+ *   2  mode-product routine per tensor-index dimension n, largest first:
+ *      the register-fibre product (n <= 32 complex64 / 16 complex128) or
+ *      the shared-memory-staged one;
+ *   4  with 2, in TTN_MIXED also the tcgen05 tensor-core product (3xTF32)
+ *      for n <= 48.
+ * tuned_ms (may be NULL) receives the time of `steps` steps with the chosen
+ * configuration.  The choice changes results only through rounding.
+ * Errors: TTN_E_INVALID (steps outside 1..1000), TTN_E_STATE (no
+ * Hamiltonian), device failures as for ttn_step. */
+ttn_status ttn_autotune(ttn_ctx* ctx, double dt, int steps, int flags, double* tuned_ms);
+
+/* The configuration in use: thread blocks per instance, the mode-product
+ * routine per dimension (variants[0..64]: 0 default, 1 staged, 2 tensor
+ * cores), and the last ttn_autotune's record: time of its steps with the
+ * chosen and with the initial configuration (ms) and the trials run.  Any
+ * output pointer may be NULL. */
+ttn_status ttn_tuning(const ttn_ctx* ctx, int* blocks, unsigned char* variants, double* tuned_ms,
+                      double* default_ms, int* trials);
+
+/* Set the configuration ttn_tuning reports (to reuse one context's tuning
+ * for others of the same shape): blocks as for ttn_set_cluster, variants
+ * [65] (may be NULL: unchanged) with entries 0, 1 or 2.  TTN_E_INVALID for
+ * other values. */
+ttn_status ttn_set_tuning(ttn_ctx* ctx, int blocks, const unsigned char* variants);
+
+/* One mode product of the mixed-precision bulk alone (kernel-level entry
+ * point, like ttn_heff_apply; the contraction of Sec. II.C Eq. psi_eom_1
+ * along one tensor index):
+ *     y[l, p, r] = w sum_m M[p, m] x[l, m, r]   (+ y[l, p, r] if accumulate)
+ * for an L x n x R complex64 tensor x (interleaved float pairs, row-major)
+ * and an n x n complex64 matrix M, all device pointers; w = wr + i wi.
+ * tensor_cores = 1: tcgen05 tensor cores with 3xTF32 split products and FP32
+ * accumulation (x = hi + lo with hi its TF32 rounding; hi*hi + hi*lo + lo*hi),
+ * one block per SM over tiles of 128 fibres; 0: the FFMA routine the sweep
+ * uses (one block).  1 <= n <= 64.  Runs on `stream` and waits.
+ * Errors through ttn_last_error(NULL); TTN_E_TIMEOUT if a tensor-core
+ * operation did not complete within its bounded wait. */
+ttn_status ttn_mode_product_c64(void* stream, int64_t L, int n, int64_t R, const void* M, const void* x, void* y,
+                                double wr, double wi, int accumulate, int tensor_cores);
+
 /* Measured arithmetic peaks of the current device (no counterpart in the
  * paper: the denominators of the roofline the sweep kernel is judged
  * against).  fp32_tflops / fp64_tflops receive the sustained rate of fused

@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <set>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -81,6 +82,11 @@ TtnInstance ttn::make_instance(ttn_ctx* c, const DevProgram& p) {
     in.spawn_out = (double*)(c->d_state + c->plan.spawn_out_off);
     in.spawn_ws = c->d_state + c->plan.spawn_ws_off;
     in.spawn_kmax = c->plan.spawn_kmax;
+    in.use_tc = 0;
+    for (int n = 0; n <= TTN_MAXCHI; ++n) {
+        in.mp_variant[n] = c->mp_variant[n];
+        in.use_tc |= c->mp_variant[n] == 2 && c->precision == TTN_MIXED;
+    }
     return in;
 }
 
@@ -806,6 +812,7 @@ ttn_status ttn_ground_state(ttn_ctx* c, int nsweeps, double* energies) {
             CK(cudaMemcpyAsync(&energies[i], c->d_state + c->plan.scal_off + 64, sizeof(double),
                                cudaMemcpyDeviceToHost, c->stream), "energy copy");
             CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+            energies[i] += c->plan.e_shift;
         }
     }
     return TTN_OK;
@@ -864,7 +871,7 @@ ttn_status ttn_norm_energy(ttn_ctx* c, double* norm2, ttn_c128* energy) {
     if (norm2) *norm2 = sc[0];
     if (energy) {
         if (!c->has_h) return fail(c, TTN_E_STATE, "no Hamiltonian set");
-        energy->re = sc[2] / sc[0];
+        energy->re = sc[2] / sc[0] + c->plan.e_shift;     // the bulk works with H - e_shift
         energy->im = sc[3] / sc[0];
     }
     return TTN_OK;
@@ -1074,6 +1081,155 @@ ttn_status ttn_set_cluster(ttn_ctx* c, int blocks) {
 ttn_status ttn_get_cluster(const ttn_ctx* c, int* blocks) {
     if (!c || !blocks) return fail(nullptr, TTN_E_INVALID, "NULL argument");
     *blocks = ttn::ctx_cluster(c);
+    return TTN_OK;
+}
+
+// Autotuning: time whole steps of the context's own problem for candidate
+// launch shapes and mode-product routines, starting every trial from the
+// same snapshot of everything a step modifies (state arena: tensors, bond
+// buffer, workspace, counters; operator arena: environment and channel
+// matrices), and keep the fastest.  The context ends exactly as it began.
+ttn_status ttn_autotune(ttn_ctx* c, double dt, int steps, int flags, double* tuned_ms) {
+    ttn_status u = usable(c); if (u) return u;
+    if (!c->has_h) return fail(c, TTN_E_STATE, "no Hamiltonian set");
+    if (steps < 1 || steps > 1000 || !std::isfinite(dt)) return fail(c, TTN_E_INVALID, "need 1 <= steps <= 1000, finite dt");
+    u = ready(c); if (u) return u;
+    const size_t slot_bytes = ops_layout(c->plan).slot_bytes;
+    char *snap_s = nullptr, *snap_o = nullptr;
+    cudaError_t ae = dev_alloc(c, &snap_s, c->state_bytes);
+    if (ae == cudaSuccess) ae = dev_alloc(c, &snap_o, std::max<size_t>(slot_bytes, 256));
+    if (ae != cudaSuccess) { dev_free(c, snap_s); return alloc_fail(c, ae, "autotune snapshot"); }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    ttn_status st = TTN_OK;
+    auto restore = [&]() -> cudaError_t {
+        cudaError_t e = cudaMemcpyAsync(c->d_state, snap_s, c->state_bytes, cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess && slot_bytes)
+            e = cudaMemcpyAsync(c->d_ops, snap_o, slot_bytes, cudaMemcpyDeviceToDevice, c->stream);
+        return e;
+    };
+    auto trial = [&](double* ms) -> ttn_status {
+        cudaError_t e = restore();
+        TtnInstance in = make_instance(c, c->step_p);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_inst, &in, sizeof(in), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+        if (e == cudaSuccess)
+            e = (cudaError_t)ttn_launch_program(c->precision, ttn::ctx_cluster(c), c->d_inst, 1, dt, steps, c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "autotune launch");
+        ttn_status s2 = check_status(c);
+        if (s2) return s2;
+        float f = 0.f;
+        cudaEventElapsedTime(&f, e0, e1);
+        *ms = f;
+        c->tune_trials++;
+        return TTN_OK;
+    };
+    do {
+        cudaError_t e = cudaMemcpyAsync(snap_s, c->d_state, c->state_bytes, cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess && slot_bytes)
+            e = cudaMemcpyAsync(snap_o, c->d_ops, slot_bytes, cudaMemcpyDeviceToDevice, c->stream);
+        if (e != cudaSuccess) { st = cuda_fail(c, e, "autotune snapshot"); break; }
+        c->tune_trials = 0;
+        double best = 0.0;
+        if ((st = trial(&best))) break;           // the configuration as given
+        c->tune_default_ms = best;
+        if (flags & 1) {                           // block count
+            const int need = c->plan.max_chi > ttn::kSoloMaxDim ? 2 : 1;
+            int best_b = c->cluster_req;
+            for (int b = need; b <= TTN_MAX_CLUSTER && !st; b *= 2) {
+                if (b > 1) {
+                    int act = 0;
+                    if (ttn_cluster_capacity(c->precision, b, &act) != 0 || act < 1) { cudaGetLastError(); continue; }
+                }
+                const int keep = c->cluster_req;
+                c->cluster_req = b;
+                double ms = 0.0;
+                st = trial(&ms);
+                if (!st && ms < best) { best = ms; best_b = b; }
+                c->cluster_req = keep;
+            }
+            if (st) break;
+            c->cluster_req = best_b;
+        }
+        if (flags & 2) {                           // mode-product routine per dimension, largest first
+            std::set<int> dims;
+            for (int z = 0; z < c->tree.n; ++z)
+                for (int d : c->tree.dims[z]) if (d >= 4) dims.insert(d);
+            const int fibre_lim = c->precision == TTN_MIXED ? 32 : 16;
+            for (auto it = dims.rbegin(); it != dims.rend() && !st; ++it) {
+                const int n = *it;
+                std::vector<int> cands;
+                if (n <= fibre_lim) cands.push_back(1);                        // staged instead of fibre
+                if ((flags & 4) && c->precision == TTN_MIXED && n <= 48) cands.push_back(2);   // tensor cores
+                const unsigned char keep = c->mp_variant[n];
+                unsigned char best_v = keep;
+                for (int v : cands) {
+                    c->mp_variant[n] = (unsigned char)v;
+                    double ms = 0.0;
+                    st = trial(&ms);
+                    if (st) break;
+                    if (ms < best) { best = ms; best_v = (unsigned char)v; }
+                }
+                c->mp_variant[n] = best_v;
+            }
+            if (st) break;
+        }
+        c->tune_ms = best;
+        if (tuned_ms) *tuned_ms = best;
+        cudaError_t r = restore();
+        if (r == cudaSuccess) r = cudaStreamSynchronize(c->stream);
+        if (r != cudaSuccess) st = cuda_fail(c, r, "autotune restore");
+    } while (false);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(c->stream);
+    dev_free(c, snap_s);
+    dev_free(c, snap_o);
+    return st;
+}
+
+ttn_status ttn_set_tuning(ttn_ctx* c, int blocks, const unsigned char* variants) {
+    if (!c) return fail(nullptr, TTN_E_INVALID, "ctx is NULL");
+    if (blocks < 0 || blocks > TTN_MAX_CLUSTER || (blocks & (blocks - 1)) != 0)
+        return fail(c, TTN_E_INVALID, "blocks must be 0 (automatic), 1, 2, 4, 8 or 16");
+    if (variants)
+        for (int n = 0; n <= TTN_MAXCHI; ++n)
+            if (variants[n] > 2) return fail(c, TTN_E_INVALID, "mode-product variants are 0, 1 or 2");
+    c->cluster_req = blocks;
+    if (variants) std::memcpy(c->mp_variant, variants, TTN_MAXCHI + 1);
+    return TTN_OK;
+}
+
+ttn_status ttn_tuning(const ttn_ctx* c, int* blocks, unsigned char* variants, double* tuned_ms, double* default_ms,
+                      int* trials) {
+    if (!c) return fail(nullptr, TTN_E_INVALID, "ctx is NULL");
+    if (blocks) *blocks = ttn::ctx_cluster(c);
+    if (variants) std::memcpy(variants, c->mp_variant, TTN_MAXCHI + 1);
+    if (tuned_ms) *tuned_ms = c->tune_ms;
+    if (default_ms) *default_ms = c->tune_default_ms;
+    if (trials) *trials = c->tune_trials;
+    return TTN_OK;
+}
+
+ttn_status ttn_mode_product_c64(void* stream, int64_t L, int n, int64_t R, const void* M, const void* x, void* y,
+                                double wr, double wi, int accumulate, int tensor_cores) {
+    if (L < 1 || R < 1 || n < 1 || n > TTN_MAXCHI || !M || !x || !y)
+        return fail(nullptr, TTN_E_INVALID, "need L, R >= 1, 1 <= n <= 64 and device pointers");
+    if (tensor_cores && n > 64) return fail(nullptr, TTN_E_INVALID, "tensor-core mode product: n <= 64");
+    cudaStream_t s = (cudaStream_t)stream;
+    int* d_status = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&d_status, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_status, 0, sizeof(int), s);
+    if (e == cudaSuccess)
+        e = (cudaError_t)ttn_launch_mode_product(tensor_cores, L, n, R, M, x, y, wr, wi, accumulate, d_status, s);
+    int st = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&st, d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (d_status) cudaFreeAsync(d_status, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(nullptr, TTN_E_CUDA, std::string("mode product: ") + cudaGetErrorString(e));
+    if (st == 5) return fail(nullptr, TTN_E_TIMEOUT, "tensor-core mode product: an MMA did not complete in time");
     return TTN_OK;
 }
 

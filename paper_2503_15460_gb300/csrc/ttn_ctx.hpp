@@ -65,6 +65,12 @@ struct ttn_ctx {
     // Thread blocks per instance: 0 = chosen from the plan, 1 = one block,
     // 2..16 = a thread-block cluster of that size.
     int cluster_req = 0;
+    // Mode-product routine per dimension (TtnInstance::mp_variant), and the
+    // autotuner's record: step time of the chosen configuration and of the
+    // default one (ms), candidates timed.
+    unsigned char mp_variant[TTN_MAXCHI + 1] = {0};
+    double tune_ms = 0.0, tune_default_ms = 0.0;
+    int tune_trials = 0;
 };
 
 namespace ttn {

@@ -28,6 +28,7 @@
 #include <stdint.h>
 
 #include "ttn_program.h"
+#include "ttn_tc.cuh"
 
 namespace {
 
@@ -56,6 +57,18 @@ __device__ __forceinline__ void count_flops_t(double f) {
         if (sizeof(T) == 16) s_flops64 += f;
     }
 }
+
+// Mode-product routine per dimension for the instance being run (copied
+// from TtnInstance::mp_variant at kernel start; zero = default rule).
+__shared__ unsigned char s_mpv[TTN_MAXCHI + 1];
+// Tensor-core state of the block when its instance uses the tcgen05
+// product: allocated tensor-memory columns, the MMA-completion mbarrier and
+// its phase, and the status word a lost MMA is reported to.
+__shared__ int s_tc_on;
+__shared__ uint32_t s_tc_taddr;
+__shared__ uint32_t s_tc_phase;
+__shared__ __align__(8) uint64_t s_tc_bar;
+__shared__ int* s_tc_status;
 
 // Sub-phase cycle counters (thread 0 of the counting block).
 __shared__ unsigned long long s_sub[8];
@@ -142,6 +155,27 @@ __device__ __forceinline__ void cfmaconj(float2& acc, float2 a, float2 b) {
 template <class T> __device__ __forceinline__ T czero();
 template <> __device__ __forceinline__ double2 czero<double2>() { return make_double2(0.0, 0.0); }
 template <> __device__ __forceinline__ float2 czero<float2>() { return make_float2(0.f, 0.f); }
+
+// Long sums of complex64 products are accumulated in short blocks whose
+// FP32 partials are folded into a compensated running sum (s, c): Knuth's
+// TwoSum keeps the rounding error of each fold exactly, so the error of the
+// whole sum is that of one block (a few eps) instead of growing with its
+// length, at 6 FP32 additions per fold -- while an FP64 accumulator would
+// cost 64 FFMA issue slots per add on this part.  complex128 sums are
+// plain (c stays unused).
+__device__ __forceinline__ void two_sum_into(float& s, float& c, float b) {
+    const float t = s + b;
+    const float bp = t - s;
+    c += (s - (t - bp)) + (b - bp);
+    s = t;
+}
+__device__ __forceinline__ void fold(float2& s, float2& c, float2 b) {
+    two_sum_into(s.x, c.x, b.x);
+    two_sum_into(s.y, c.y, b.y);
+}
+__device__ __forceinline__ void fold(double2& s, double2&, double2 b) { s.x += b.x; s.y += b.y; }
+__device__ __forceinline__ double2 folded(float2 s, float2 c) { return make_double2((double)s.x + c.x, (double)s.y + c.y); }
+__device__ __forceinline__ double2 folded(double2 s, double2) { return s; }
 
 __device__ __forceinline__ double2 warp_sum(double2 v) {
     for (int o = 16; o > 0; o >>= 1) {
@@ -280,10 +314,15 @@ __device__ int team_flag(int v, Smem& sm, const TM& tm) {
 
 template <class T, class TM>
 __device__ double2 team_dot(const T* a, const T* b, int64_t n, Smem& sm, const TM& tm) {
-    T acc = czero<T>();
-    for (int64_t i = tm.tid(); i < n; i += tm.nthr()) cfmaconj(acc, a[i], b[i]);
+    T acc = czero<T>(), cmp = czero<T>();
+    const int64_t ts = tm.nthr();
+    for (int64_t i0 = tm.tid(); i0 < n; i0 += 16 * ts) {
+        T blk = czero<T>();
+        for (int64_t i = i0, k = 0; k < 16 && i < n; ++k, i += ts) cfmaconj(blk, a[i], b[i]);
+        fold(acc, cmp, blk);
+    }
     count_flops_t<T>(8.0 * n);
-    return team_sum(cd(acc), sm, tm);
+    return team_sum(folded(acc, cmp), sm, tm);
 }
 
 // ---------------------------------------------------------------------------
@@ -407,21 +446,24 @@ __device__ void mode_prod_staged(T* out, const T* in, int64_t L, int n, int64_t 
     const T wt = cT<T>(w);
     const int f = threadIdx.x % FT, pb = threadIdx.x / FT;
     const int p0 = pb * PB;
+    const int MS = NT / FT;                          // fibre loads: thread -> (fibre f, m = pb, pb + MS, ...)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int64_t tile = tm.rank(); tile < ntile; tile += tm.size()) {
         const int64_t f0 = tile * FT;
         const int nf = (int)((F - f0) < FT ? (F - f0) : FT);
         __syncthreads();
         if (R == 1) {
-            for (int i = threadIdx.x; i < nf * n; i += NT) {
-                const int ff = i / n, m = i - ff * n;
-                Xs[m * ld + ff] = in[(f0 + ff) * n + m];
+            // whole fibres are contiguous rows: warps take fibres, lanes the row
+            for (int ff = warp; ff < nf; ff += NT / 32) {
+                const T* src = in + (f0 + ff) * n;
+                for (int m = lane; m < n; m += 32) Xs[m * ld + ff] = src[m];
             }
-        } else {
-            for (int i = threadIdx.x; i < nf * n; i += NT) {
-                const int m = i / nf, ff = i - m * nf;
-                const int64_t g = f0 + ff, l = g / R, r = g - l * R;
-                Xs[m * ld + ff] = in[(l * n + m) * R + r];
-            }
+        } else if (f < nf && pb < MS) {
+            // consecutive threads take consecutive fibres (consecutive r); one
+            // division per tile locates the fibre
+            const int64_t g = f0 + f, l = g / R, r = g - l * R;
+            const T* src = in + l * n * R + r;
+            for (int m = pb; m < n; m += MS) Xs[m * ld + f] = src[(int64_t)m * R];
         }
         __syncthreads();
         if (pb < npb && f < nf) {
@@ -451,14 +493,32 @@ __device__ void mode_prod_staged(T* out, const T* in, int64_t L, int n, int64_t 
 }
 
 template <class T, class TM>
-__device__ void mode_prod(T* out, const T* in, int64_t L, int nin, int nout, int64_t R, const T* M, bool transM,
+__device__ __noinline__ void mode_prod(T* out, const T* in, int64_t L, int nin, int nout, int64_t R, const T* M, bool transM,
                           double2 w, bool accumulate, const TM& tm) {
     count_flops_t<T>(8.0 * (double)(L * nout * R) * nin);
     if (transM || nin != nout) {
         mode_prod_simple(out, in, L, nin, nout, R, M, transM, w, accumulate, tm);
         return;
     }
-    if (nin > (sizeof(T) == 16 ? 16 : 32)) {
+    if constexpr (sizeof(T) == 8) {
+        // tensor cores (3xTF32) where the variant table asks for them and the
+        // operands fit the staging area
+        constexpr int stage = TM::wide ? kStageBytesClu : kStageBytes;
+        if (s_mpv[nin] == 2 && s_tc_on && tc_fits(nin, stage)) {
+            uint32_t ph = s_tc_phase;
+            const int err = tc_mode_prod<TM::NT>((float2*)out, (const float2*)in, L, nin, R, (const float2*)M, w,
+                                                 accumulate, dyn_smem, stage, s_tc_taddr, &s_tc_bar, ph, tm.rank(),
+                                                 tm.size());
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                s_tc_phase = ph;
+                if (err && s_tc_status) atomicExch(s_tc_status, 5);    // TTN_E_TIMEOUT
+            }
+            tm.sync();
+            return;
+        }
+    }
+    if (nin > (sizeof(T) == 16 ? 16 : 32) || s_mpv[nin] != 0) {
         mode_prod_staged<T, (sizeof(T) == 16 ? 4 : 8)>(out, in, L, nin, R, M, w, accumulate, tm);
         return;
     }
@@ -577,7 +637,7 @@ __device__ void heff_apply(T* out, const T* in, T* t1, T* t2, T* t3, const Shape
 // deals the tiles out to its blocks and adds the blocks' partials in rank
 // order.
 template <class T, class TM>
-__device__ void gram_acc(T* G, const T* X, const T* Y, const Shape& sh, int k, double2 w, const TM& tm) {
+__device__ __noinline__ void gram_acc(T* G, const T* X, const T* Y, const Shape& sh, int k, double2 w, const TM& tm) {
     constexpr int NT = TM::NT;
     const int chi = sh.d[k];
     const int64_t L = sh.before(k), R = sh.after(k), O = L * R;
@@ -592,17 +652,18 @@ __device__ void gram_acc(T* G, const T* X, const T* Y, const Shape& sh, int k, d
     if (groups > 8) groups = 8;
     const int tid = threadIdx.x;
     const bool active = tid < ntile * groups || ntile > NT;
-    T acc[2][2][2];
+    T acc[2][2][2], cmp[2][2][2];                // running sums and their compensations
     const int nrep = (ntile + NT - 1) / NT;      // tiles per thread when chi is large
 #pragma unroll
     for (int q = 0; q < 2; ++q)
 #pragma unroll
         for (int i = 0; i < 2; ++i)
 #pragma unroll
-            for (int j = 0; j < 2; ++j) acc[q][i][j] = czero<T>();
+            for (int j = 0; j < 2; ++j) { acc[q][i][j] = czero<T>(); cmp[q][i][j] = czero<T>(); }
     const int g = (ntile >= NT) ? 0 : tid / ntile;
     const int gcount = (ntile >= NT) ? 1 : groups;
     const int64_t ntiles = (O + OT - 1) / OT;
+    const int SA = NT / OT, soo = tid % OT, sa = tid / OT;    // staging: thread -> (position, a = sa, sa + SA, ...)
     for (int64_t ti = tm.rank(); ti < ntiles; ti += tm.size()) {
         const int64_t o0 = ti * OT;
         const int nt = (int)((O - o0) < OT ? (O - o0) : OT);
@@ -610,13 +671,14 @@ __device__ void gram_acc(T* G, const T* X, const T* Y, const Shape& sh, int k, d
             const T* xs = X + o0 * chi;
             const T* ys = Y + o0 * chi;
             for (int i = tid; i < nt * chi; i += NT) { Xs[i] = xs[i]; Ys[i] = ys[i]; }
-        } else {
-            for (int i = tid; i < nt * chi; i += NT) {
-                const int oo = i % nt, a = i / nt;
-                const int64_t o = o0 + oo, l = o / R, r = o - (o / R) * R;
-                const int64_t src = (l * chi + a) * R + r;
-                Xs[oo * chi + a] = X[src];
-                Ys[oo * chi + a] = Y[src];
+        } else if (soo < nt && sa < SA) {
+            // consecutive threads take consecutive positions (consecutive r);
+            // one division per tile locates the position
+            const int64_t o = o0 + soo, l = o / R, r = o - l * R;
+            const int64_t base = l * chi * R + r;
+            for (int a = sa; a < chi; a += SA) {
+                Xs[soo * chi + a] = X[base + (int64_t)a * R];
+                Ys[soo * chi + a] = Y[base + (int64_t)a * R];
             }
         }
         __syncthreads();
@@ -628,14 +690,17 @@ __device__ void gram_acc(T* G, const T* X, const T* Y, const Shape& sh, int k, d
                 if (tile >= ntile) break;
                 const int a0 = 2 * (tile / tn), b0 = 2 * (tile % tn);
                 const bool a1ok = a0 + 1 < chi, b1ok = b0 + 1 < chi;
+                T p00 = czero<T>(), p01 = czero<T>(), p10 = czero<T>(), p11 = czero<T>();
                 for (int oo = g; oo < nt; oo += gcount) {
                     const T x0 = Xs[oo * chi + a0];
                     const T x1 = a1ok ? Xs[oo * chi + a0 + 1] : czero<T>();
                     const T y0 = Ys[oo * chi + b0];
                     const T y1 = b1ok ? Ys[oo * chi + b0 + 1] : czero<T>();
-                    cfmaconj(acc[q][0][0], x0, y0); cfmaconj(acc[q][0][1], x0, y1);
-                    cfmaconj(acc[q][1][0], x1, y0); cfmaconj(acc[q][1][1], x1, y1);
+                    cfmaconj(p00, x0, y0); cfmaconj(p01, x0, y1);
+                    cfmaconj(p10, x1, y0); cfmaconj(p11, x1, y1);
                 }
+                fold(acc[q][0][0], cmp[q][0][0], p00); fold(acc[q][0][1], cmp[q][0][1], p01);
+                fold(acc[q][1][0], cmp[q][1][0], p10); fold(acc[q][1][1], cmp[q][1][1], p11);
             }
         }
         __syncthreads();
@@ -651,7 +716,12 @@ __device__ void gram_acc(T* G, const T* X, const T* Y, const Shape& sh, int k, d
             const int a0 = 2 * (tile / tn), b0 = 2 * (tile % tn);
             for (int i = 0; i < 2; ++i)
                 for (int j = 0; j < 2; ++j)
-                    if (a0 + i < chi && b0 + j < chi) Pp[((int64_t)g * chi + a0 + i) * chi + b0 + j] = acc[q][i][j];
+                    if (a0 + i < chi && b0 + j < chi) {
+                        T v = acc[q][i][j];
+                        v.x += cmp[q][i][j].x;       // (complex128: cmp is zero)
+                        v.y += cmp[q][i][j].y;
+                        Pp[((int64_t)g * chi + a0 + i) * chi + b0 + j] = v;
+                    }
         }
     }
     __syncthreads();
@@ -998,7 +1068,7 @@ __device__ void qr_mode_clu(T* A, const Shape& sh, int k, double2* Wc, double2* 
 }
 
 template <class T, class TM>
-__device__ void qr_mode(T* A, const Shape& sh, int k, double2* Wc, double2* Qc, double tol, Smem& sm, const TM& tm) {
+__device__ __noinline__ void qr_mode(T* A, const Shape& sh, int k, double2* Wc, double2* Qc, double tol, Smem& sm, const TM& tm) {
     if constexpr (TM::wide) qr_mode_clu(A, sh, k, Wc, Qc, tol, sm, tm);
     else qr_mode_solo(A, sh, k, Wc, Qc, tol, sm, tm);
 }
@@ -1012,11 +1082,17 @@ __device__ __forceinline__ double2 qr_R(const double2* Wc, int64_t m, int a, int
 // ---------------------------------------------------------------------------
 // Small projected exponential: sm.y = exp(-i tau H_m) e_0 (warp 0 of every
 // block; the blocks of a cluster compute the same values).
-// Scaling into substeps of 1-norm <= 1, each summed as a Taylor series on
-// the vector (Moler & Van Loan, "Nineteen dubious ways", method 1 with
-// scaling); for a tridiagonal H only the band is used.
+// Scaling into s substeps of 1-norm theta <= 4, each summed as a Taylor
+// series on the vector (Moler & Van Loan, "Nineteen dubious ways", method 1
+// with scaling) with the number of terms k chosen so that theta^(k+1)/(k+1)!
+// < 1e-17 (k = 14, 18, 24, 32 for theta <= 1/2, 1, 2, 4); a substep's series
+// stops early once the 1-norm bound on the remaining terms is below 1e-18 of
+// the partial sum.  The work is
+// FP64 (two lanes per SM on this part), so fewer, longer substeps matter:
+// 8 nu term evaluations instead of 18 nu for 1-norm nu.  For a tridiagonal
+// H only the band is used, for an upper Hessenberg one only j >= i - 1.
 // ---------------------------------------------------------------------------
-__device__ void small_expm(Smem& sm, int m, double tau, bool band) {
+__device__ __noinline__ void small_expm(Smem& sm, int m, double tau, bool band) {
     if ((threadIdx.x >> 5) != 0) return;
     const int i = threadIdx.x & 31;
     double colsum = 0.0;
@@ -1028,9 +1104,10 @@ __device__ void small_expm(Smem& sm, int m, double tau, bool band) {
         __syncwarp();
         return;
     }
-    // substeps of 1-norm <= 1; 18 Taylor terms leave a truncation below 1/19! ~ 8e-18
-    int s = (int)ceil(nrm);
+    int s = (int)ceil(nrm / 4.0);
     if (s < 1) s = 1;
+    const double theta = nrm / s;
+    const int kterms = theta <= 0.5 ? 14 : theta <= 1.0 ? 18 : theta <= 2.0 ? 24 : 32;
     const double h = tau / s;
     double2 y = make_double2(i == 0 ? 1.0 : 0.0, 0.0);
     const int jlo = max(0, i - 1);
@@ -1038,7 +1115,7 @@ __device__ void small_expm(Smem& sm, int m, double tau, bool band) {
     for (int step = 0; step < s; ++step) {
         double2 term = y, acc = y;
 #pragma unroll 1
-        for (int kk = 1; kk <= 18; ++kk) {
+        for (int kk = 1; kk <= kterms; ++kk) {
             sm.u[i] = term;
             __syncwarp();
             double2 nt = make_double2(0.0, 0.0);
@@ -1048,6 +1125,13 @@ __device__ void small_expm(Smem& sm, int m, double tau, bool band) {
             const double f = h / kk;
             term = (i < m) ? make_double2(nt.y * f, -nt.x * f) : make_double2(0.0, 0.0);
             acc = cadd(acc, term);
+            // ||t_{k+1}||_1 <= theta / (k+1) ||t_k||_1, so once k >= 2 theta the
+            // tail is below the current term; stop when m max|t| <= 1e-18 max|acc|
+            // (the same decision in every lane and every block of a cluster)
+            if ((kk & 1) == 0 && kk >= 2.0 * theta + 1.0) {
+                const double t2 = warp_max(cabs2(term)), a2 = warp_max(cabs2(acc));
+                if ((double)m * m * t2 <= 1e-36 * a2) break;
+            }
         }
         y = acc;
     }
@@ -1064,7 +1148,7 @@ __device__ void small_expm(Smem& sm, int m, double tau, bool band) {
 // The rotation parameters of a round are computed by every block (in its
 // own shared memory); the rotations themselves are dealt out to the team.
 template <class TM>
-__device__ void jacobi_eigh(double2* A, double2* Vm, int n, Smem& sm, const TM& tm) {
+__device__ __noinline__ void jacobi_eigh(double2* A, double2* Vm, int n, Smem& sm, const TM& tm) {
     constexpr int NT = TM::NT;
     const int tid = threadIdx.x;
     for (int i = tm.tid(); i < n * n; i += tm.nthr()) Vm[i] = make_double2(i / n == i % n ? 1.0 : 0.0, 0.0);
@@ -1205,15 +1289,21 @@ __device__ int krylov_once(TS* x, const Shape& sh, const TtnEntry* es, int ne, c
             for (int i0 = 0; i0 <= j; i0 += 4) {
                 const int nb = (j + 1 - i0) < 4 ? (j + 1 - i0) : 4;
                 TB acc[4] = {czero<TB>(), czero<TB>(), czero<TB>(), czero<TB>()};
-                for (int64_t e = t0; e < S; e += ts) {
-                    const TB we = w[e];
+                TB cmp[4] = {czero<TB>(), czero<TB>(), czero<TB>(), czero<TB>()};
+                for (int64_t e0 = t0; e0 < S; e0 += 16 * ts) {
+                    TB blk[4] = {czero<TB>(), czero<TB>(), czero<TB>(), czero<TB>()};
+                    for (int64_t e = e0, k = 0; k < 16 && e < S; ++k, e += ts) {
+                        const TB we = w[e];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        if (q < nb) cfmaconj(acc[q], V[(int64_t)(i0 + q) * smax + e], we);
+                        for (int q = 0; q < 4; ++q)
+                            if (q < nb) cfmaconj(blk[q], V[(int64_t)(i0 + q) * smax + e], we);
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) fold(acc[q], cmp[q], blk[q]);
                 }
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const double2 d = warp_sum(cd(acc[q]));
+                    const double2 d = warp_sum(folded(acc[q], cmp[q]));
                     if (lane == 0 && q < nb) sm.gsw[warp][i0 + q] = d;
                 }
             }
@@ -1273,9 +1363,13 @@ __device__ int krylov_once(TS* x, const Shape& sh, const TtnEntry* es, int ne, c
             for (int i = 0; i + 1 < j; ++i) sm.H[i * TTN_KMAX + j] = make_double2(0.0, 0.0);
             if (j > 0) sm.H[(j - 1) * TTN_KMAX + j] = sm.H[j * TTN_KMAX + (j - 1)];
         }
-        TB nwt = czero<TB>();
-        for (int64_t e = t0; e < S; e += ts) cfmaconj(nwt, w[e], w[e]);
-        const double hnext = sqrt(team_sum(cd(nwt), sm, tm).x);
+        TB nwt = czero<TB>(), nwc = czero<TB>();
+        for (int64_t e0 = t0; e0 < S; e0 += 16 * ts) {
+            TB blk = czero<TB>();
+            for (int64_t e = e0, k = 0; k < 16 && e < S; ++k, e += ts) cfmaconj(blk, w[e], w[e]);
+            fold(nwt, nwc, blk);
+        }
+        const double hnext = sqrt(team_sum(folded(nwt, nwc), sm, tm).x);
         if (threadIdx.x == 0) sm.H[(j + 1) * TTN_KMAX + j] = make_double2(hnext, 0.0);
         __syncthreads();
         sub_stop(1, tgs);
@@ -1426,7 +1520,7 @@ __device__ void small_gemm(double2* C, const double2* A, const double2* B, int m
 // E = X'^dag X' = V L V^dag and F = V L^{-1/2} (numerically nonzero part),
 // T = F^dag E C E F is Hermitian and its eigenvector w gives u = X' F w.
 template <class TS, class TB, class TM>
-__device__ void spawn_op(const TtnOp& op, const TtnInstance& in, Smem& sm, TB* V, int64_t smax, TB* t1, TB* t2,
+__device__ __noinline__ void spawn_op(const TtnOp& op, const TtnInstance& in, Smem& sm, TB* V, int64_t smax, TB* t1, TB* t2,
                          double2* Wc, double2* Qc, const TM& tm) {
     const int t0 = tm.tid(), ts = tm.nthr();
     Shape shz, shc;
@@ -1818,6 +1912,14 @@ __device__ void run_op(const TtnOp& op, const TtnInstance& in, double dt, Smem& 
     case TTN_OP_SPAWN:
         spawn_op<TS, TB>(op, in, sm, V, in.smax, t1, t2, Wc, Qc, tm);
         break;
+    case TTN_OP_PHASE: {             // a <- exp(-i tau_coef dt) a
+        TS* A = (TS*)op.a;
+        const double th = op.tau_coef * dt;
+        const double2 f = make_double2(cos(th), -sin(th));
+        for (int64_t i = t0; i < sh.size(); i += ts) A[i] = cT<TS>(cmul(f, cd(A[i])));
+        tm.sync();
+        break;
+    }
     case TTN_OP_STEP_END:
         if (lead) {
             const int s = *in.steps_done;
@@ -1881,7 +1983,19 @@ __global__ void __launch_bounds__(TM::NT, TM::wide ? 1 : 2) program_kernel(const
         for (int i = 0; i < 8; ++i) s_sub[i] = 0;
         s_t0 = global_ns();
     }
+    for (int i = threadIdx.x; i <= TTN_MAXCHI; i += TM::NT) s_mpv[i] = in.mp_variant[i];
+    const bool use_tc = sizeof(TB) == 8 && in.use_tc != 0;
+    if (threadIdx.x == 0) { s_tc_on = use_tc ? 1 : 0; s_tc_phase = 0; s_tc_status = in.status; }
+    if (use_tc) {
+        if ((threadIdx.x >> 5) == 0) tc_alloc(&s_tc_taddr, kTcCols);
+        if (threadIdx.x == 0) {
+            tc_mbar_init(&s_tc_bar, 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        tc_fence_before();
+    }
     tm.sync();
+    if (use_tc) tc_fence_after();
     int rep = 0;
     bool stopped = false;
     while (rep < nr) {
@@ -1913,6 +2027,11 @@ __global__ void __launch_bounds__(TM::NT, TM::wide ? 1 : 2) program_kernel(const
         r.status = *((volatile int*)in.status);
         r.elapsed_ns = global_ns() - s_t0;
         rep_out[b] = r;
+    }
+    if (use_tc) {                             // every MMA was waited for: free the tensor memory
+        tc_fence_before();
+        __syncthreads();
+        if ((threadIdx.x >> 5) == 0) tc_dealloc(s_tc_taddr, kTcCols);
     }
     if constexpr (TM::wide) tm.sync();        // no block leaves while others may read its shared memory
 }

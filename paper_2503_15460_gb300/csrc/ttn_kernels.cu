@@ -17,6 +17,7 @@ __global__ void __launch_bounds__(256, 1) heff_kernel(const TtnEntry* es, int ne
                                                       const double2* x, double2* y, double2* t1, double2* t2,
                                                       double2* t3) {
     if (threadIdx.x == 0) { s_flops = 0.0; s_flops64 = 0.0; s_count = 1; }
+    for (int i = threadIdx.x; i <= TTN_MAXCHI; i += 256) s_mpv[i] = 0;
     __syncthreads();
     heff_apply(y, x, t1, t2, t3, sh, es, ne, slots, Solo<256>());
 }

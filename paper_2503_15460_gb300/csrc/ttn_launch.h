@@ -59,6 +59,14 @@ int ttn_launch_heff_noalloc(const TtnEntry* h_entries, int ne, const TtnSlot* h_
 int ttn_pipe_peak_fp32(int iters, double* tflops, double* ms, cudaStream_t stream);
 int ttn_pipe_peak_fp64(int iters, double* tflops, double* ms, cudaStream_t stream);
 
+// One complex64 mode product y[l, p, r] (+)= w sum_m M[p, m] x[l, m, r]
+// (device pointers, interleaved float pairs): tensor_cores = 1 on tcgen05
+// with 3xTF32 split products (n <= 64, one block per SM over the fibre
+// tiles), 0 by the sweep's FFMA routine (one block).  d_status (device int)
+// receives 5 if an MMA did not complete in time.
+int ttn_launch_mode_product(int tensor_cores, int64_t L, int n, int64_t R, const void* M, const void* x, void* y,
+                            double wr, double wi, int accumulate, int* d_status, cudaStream_t stream);
+
 // ---- internal: one entry point per kernel variant (own translation unit) ----
 struct TtnVariantArgs {
     const TtnInstance* insts;

@@ -30,6 +30,42 @@ namespace {
 
 int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
+// Smallest eigenvalue of a Hermitian d x d matrix (row-major) by cyclic
+// Jacobi rotations (Golub & Van Loan, Sec. 8.5, in the complex form that
+// first makes the pivot real).
+double min_eig_hermitian(std::vector<cplx> A, int d) {
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0, dia = 0.0;
+        for (int i = 0; i < d; ++i)
+            for (int j = 0; j < d; ++j) (i == j ? dia : off) += std::norm(A[i * d + j]);
+        if (off <= 1e-30 * (off + dia) || off == 0.0) break;
+        for (int p = 0; p < d; ++p)
+            for (int q = p + 1; q < d; ++q) {
+                const cplx apq = A[p * d + q];
+                const double r = std::abs(apq);
+                if (r <= 1e-300) continue;
+                const double theta = (A[q * d + q].real() - A[p * d + p].real()) / (2.0 * r);
+                const double t = (theta >= 0.0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+                const cplx e = std::conj(apq) / r;
+                for (int row = 0; row < d; ++row) {
+                    const cplx ap = A[row * d + p], aq = e * A[row * d + q];
+                    A[row * d + p] = c * ap - sn * aq;
+                    A[row * d + q] = sn * ap + c * aq;
+                }
+                const cplx ec = std::conj(e);
+                for (int col = 0; col < d; ++col) {
+                    const cplx ap = A[p * d + col], aq = ec * A[q * d + col];
+                    A[p * d + col] = c * ap - sn * aq;
+                    A[q * d + col] = sn * ap + c * aq;
+                }
+            }
+    }
+    double m = A[0].real();
+    for (int i = 1; i < d; ++i) m = std::min(m, A[i * d + i].real());
+    return m;
+}
+
 }  // namespace
 
 std::vector<int> Tree::preorder() const {
@@ -502,8 +538,16 @@ struct Builder {
                 for (int i = 0; i < d * d; ++i) loc_sum[l][i] += h->coeff[r] * h->mats[key[0].second][i];
             }
         }
-        for (int l = 0; l < n; ++l)
-            if (!loc_sum[l].empty()) phys_loc[l] = const_slot(t.phys[l], t.phys[l], loc_sum[l]);
+        for (int l = 0; l < n; ++l) {
+            if (loc_sum[l].empty()) continue;
+            if (p.esz == 8 && h->hermitian) {      // complex64 bulk: store excitation energies
+                const int d = t.phys[l];
+                const double lam = min_eig_hermitian(loc_sum[l], d);
+                for (int i = 0; i < d; ++i) loc_sum[l][i * d + i] -= lam;
+                p.e_shift += lam;
+            }
+            phys_loc[l] = const_slot(t.phys[l], t.phys[l], loc_sum[l]);
+        }
         for (int c = 1; c < n; ++c) {
             std::set<Key> ins, outs;
             for (int r = 0; r < R; ++r) {
@@ -1003,6 +1047,11 @@ std::string make_plan(const Tree& t, const Hamiltonian* h, int precision, Plan& 
         p.spawn_kmax = std::min(kmax, TTN_SPAWN_MAX_K);
         p.spawn_ws_off = p.total_bytes;
         p.total_bytes = align_up(p.total_bytes + 16 * (p.smax + 6 * (int64_t)p.spawn_kmax * p.spawn_kmax), 256);
+        if (p.e_shift != 0.0) {                    // global phase of the shift, on the root (the centre)
+            OpSpec ph = b.tensor_op(TTN_OP_PHASE, 0, 0);
+            ph.op.tau_coef = p.e_shift;
+            p.step_prog.ops.push_back(ph);
+        }
         OpSpec s;
         std::memset(&s.op, 0, sizeof(TtnOp));
         s.op.type = TTN_OP_STEP_END;

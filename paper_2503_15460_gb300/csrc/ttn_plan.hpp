@@ -68,6 +68,13 @@ struct Plan {
     std::vector<int64_t> tensor_off;
     int64_t bond_off = 0, work_off = 0, status_off = 0, steps_off = 0, stamps_off = 0, scal_off = 0, flops_off = 0, cycles_off = 0;
     int64_t smax = 0;                // elements per workspace vector
+    // Energy shift of the complex64 path: the Hermitian local operator of
+    // every leaf is stored minus its smallest eigenvalue (Sum of them =
+    // e_shift), so the bulk arithmetic works on excitation energies; the
+    // step ends with the global phase exp(-i e_shift dt) and energies are
+    // reported with e_shift added.  Zero in complex128 and for generators
+    // that are not Hermitian.
+    double e_shift = 0.0;
     int max_stamps = 0;
     int64_t total_bytes = 0;
     int max_chi = 1;

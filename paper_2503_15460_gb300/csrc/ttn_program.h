@@ -33,7 +33,8 @@ enum TtnOpType : int {
     TTN_OP_CONTRACT_VEC = 10,// a' <- contraction of tensor a with matrices on modes (vacuum projection)
     TTN_OP_STEP_END = 11,    // end of one time step (timestamp, step counter)
     TTN_OP_SPAWN = 12,       // subspace expansion test of the bond to child k (centre at a)
-    TTN_OP_EIGEN = 13        // a <- lowest eigenvector of H (entries, Hermitian), normalised; out <- eigenvalue
+    TTN_OP_EIGEN = 13,       // a <- lowest eigenvector of H (entries, Hermitian), normalised; out <- eigenvalue
+    TTN_OP_PHASE = 14        // a <- exp(-i tau_coef dt) a   (global phase of an energy shift)
 };
 
 // Status word value left by a SPAWN op that accepted new single-particle
@@ -108,6 +109,12 @@ struct TtnInstance {
     int spawn_kmax;         // largest K the workspace holds
     int nrep;               // steps this launch when the launch asks for per-instance counts
     double dt;              // time step for the same case
+    // Mode-product routine per dimension n (index n, 0..TTN_MAXCHI):
+    // 0 = default (register fibre up to 32 in complex64 / 16 in complex128,
+    // staged above), 1 = staged, 2 = tensor cores (complex64 bulk, where the
+    // operands fit the staging area; else staged).  Chosen by ttn_autotune.
+    unsigned char mp_variant[TTN_MAXCHI + 1];
+    int use_tc;             // some entry of mp_variant is 2: hold tensor memory
 };
 
 // Launch parameters read from device memory (so one captured launch can be

@@ -76,6 +76,12 @@ _sig = {
     "ttn_set_device": ([C.c_int], C.c_int),
     "ttn_set_cluster": ([_P, C.c_int], C.c_int),
     "ttn_pipe_peaks": ([_P, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
+    "ttn_autotune": ([_P, C.c_double, C.c_int, C.c_int, C.POINTER(C.c_double)], C.c_int),
+    "ttn_set_tuning": ([_P, C.c_int, np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")], C.c_int),
+    "ttn_tuning": ([_P, C.POINTER(C.c_int), np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS"),
+                    C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int)], C.c_int),
+    "ttn_mode_product_c64": ([_P, C.c_int64, C.c_int, C.c_int64, _P, _P, _P, C.c_double, C.c_double, C.c_int,
+                              C.c_int], C.c_int),
     "ttn_get_cluster": ([_P, C.POINTER(C.c_int)], C.c_int),
     "ttn_heff_apply": ([_P, C.c_int, _I32, C.c_int, _C128, _I32, C.c_int, C.POINTER(_P), _P, _P], C.c_int),
     "ttn_heff_apply_noalloc": ([_P, C.c_int, _I32, C.c_int, _C128, _I32, C.c_int, C.POINTER(_P), _P, _P], C.c_int),
@@ -290,7 +296,7 @@ def ttn_bond_dims(ctx, n_nodes=None):
 
 
 OP_NAMES = {1: "qr_down", 2: "qr_up", 3: "absorb_child", 4: "absorb_parent", 5: "env", 6: "combo",
-            7: "evolve", 8: "dot", 9: "trace", 10: "contract_vec", 11: "step_end", 12: "spawn", 13: "eigen",
+            7: "evolve", 8: "dot", 9: "trace", 10: "contract_vec", 11: "step_end", 12: "spawn", 13: "eigen", 14: "phase",
             16: "in:heff", 17: "in:gram_schmidt", 18: "in:small_expm", 19: "in:gram", 20: "in:convert"}
 
 
@@ -324,6 +330,36 @@ def ttn_heff_apply_noalloc(stream, dims, coeff, factor, mat_ptrs, x_ptr, y_ptr):
 
 def ttn_set_device(device: int):
     _check(_lib.ttn_set_device(int(device)), None)
+
+
+def ttn_mode_product_c64(stream, L, n, R, M_ptr, x_ptr, y_ptr, w=1.0, accumulate=False, tensor_cores=True):
+    """y[l, p, r] (+)= w sum_m M[p, m] x[l, m, r] on device complex64 buffers."""
+    w = complex(w)
+    _check(_lib.ttn_mode_product_c64(C.c_void_p(int(stream or 0)), int(L), int(n), int(R), C.c_void_p(int(M_ptr)),
+                                     C.c_void_p(int(x_ptr)), C.c_void_p(int(y_ptr)), w.real, w.imag,
+                                     int(bool(accumulate)), int(bool(tensor_cores))), None)
+
+
+def ttn_autotune(ctx, dt, steps=2, flags=3):
+    ms = C.c_double(0.0)
+    _check(_lib.ttn_autotune(ctx, float(dt), int(steps), int(flags), C.byref(ms)), ctx)
+    return ms.value
+
+
+def ttn_tuning(ctx):
+    b, n = C.c_int(0), C.c_int(0)
+    t, d = C.c_double(0.0), C.c_double(0.0)
+    v = np.zeros(65, dtype=np.uint8)
+    _check(_lib.ttn_tuning(ctx, C.byref(b), v, C.byref(t), C.byref(d), C.byref(n)), ctx)
+    return {"blocks": b.value, "variants": {i: int(x) for i, x in enumerate(v) if x}, "tuned_ms": t.value,
+            "default_ms": d.value, "trials": n.value}
+
+
+def ttn_set_tuning(ctx, blocks, variants):
+    v = np.zeros(65, dtype=np.uint8)
+    for n, x in (variants.items() if isinstance(variants, dict) else enumerate(variants)):
+        v[int(n)] = int(x)
+    _check(_lib.ttn_set_tuning(ctx, int(blocks), v), ctx)
 
 
 def ttn_pipe_peaks(stream=0, seconds=0.5):
@@ -522,6 +558,17 @@ class Context:
 
     def step(self, dt, nsteps=1, opts=None):
         ttn_step(self.h, dt, nsteps, opts)
+
+    def autotune(self, dt, steps=2, flags=3):
+        """Time candidate launch shapes / contraction routines on this problem
+        and keep the fastest; the state is left unchanged."""
+        return ttn_autotune(self.h, dt, steps, flags)
+
+    def tuning(self):
+        return ttn_tuning(self.h)
+
+    def set_tuning(self, blocks, variants):
+        ttn_set_tuning(self.h, blocks, variants)
 
     def set_cluster(self, blocks):
         """Thread blocks per instance: 0 = automatic, 1 = one block, 2..16 = a cluster."""
