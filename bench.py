@@ -45,6 +45,19 @@ PEAK_FP32 = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12   # TFLOP/s
 PEAK_FP64 = N_SM * FP64_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
 
+# the sources of the sweep kernel: a traffic figure counts only while they
+# are the ones it was measured on
+KERNEL_SOURCES = ("ttn_device.cuh", "ttn_tc.cuh", "ttn_variant.cuh", "ttn_var_mix_solo.cu", "ttn_program.h")
+
+
+def kernel_source_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2503_15460_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
 def measured_traffic(batch):
     """DRAM bytes of one launch (batch instance-steps) from the committed ncu
     summary, if it was measured on the current kernel source; else None."""
@@ -55,7 +68,7 @@ def measured_traffic(batch):
     except (OSError, ValueError):
         return None
     h = hashlib.sha256()
-    for f in ("ttn_kernels.cu", "ttn_program.h"):
+    for f in KERNEL_SOURCES:
         h.update(open(os.path.join(ROOT, "paper_2503_15460_gb300", "csrc", f), "rb").read())
     if h.hexdigest() != rec.get("kernel_source_sha256"):
         return None

@@ -340,6 +340,19 @@ ttn_status ttn_autotune(ttn_ctx* ctx, double dt, int steps, int flags, double* t
 ttn_status ttn_tuning(const ttn_ctx* ctx, int* blocks, unsigned char* variants, double* tuned_ms,
                       double* default_ms, int* trials);
 
+/* Operator bond dimensions of the hierarchical sum-of-products form the
+ * library built from the Hamiltonian (Sec. II.B.2): out[c] = the number of
+ * (single-particle operator, mean-field operator) pairs crossing the bond
+ * between node c and its parent -- one for the terms acting only inside the
+ * subtree of c, one for those acting only outside, and, for the terms acting
+ * on both sides, the size of a minimum vertex cover of the bipartite graph
+ * whose vertices are their distinct inside and outside parts (a term is
+ * summed into the channel of its inside part when that is in the cover,
+ * else into the channel of its outside part); out[0] = 0.  Works on
+ * host-resident contexts (no device work).  TTN_E_STATE without a
+ * Hamiltonian. */
+ttn_status ttn_operator_dims(const ttn_ctx* ctx, int* out);
+
 /* Set the configuration ttn_tuning reports (to reuse one context's tuning
  * for others of the same shape): blocks as for ttn_set_cluster, variants
  * [65] (may be NULL: unchanged) with entries 0, 1 or 2.  TTN_E_INVALID for

@@ -1190,6 +1190,14 @@ ttn_status ttn_autotune(ttn_ctx* c, double dt, int steps, int flags, double* tun
     return st;
 }
 
+ttn_status ttn_operator_dims(const ttn_ctx* c, int* out) {
+    if (!c || !out) return fail(nullptr, TTN_E_INVALID, "NULL argument");
+    if (!c->has_h) return fail(nullptr, TTN_E_STATE, "no Hamiltonian set");
+    for (int z = 0; z < c->tree.n; ++z)
+        out[z] = z < (int)c->plan.op_bond_dim.size() ? c->plan.op_bond_dim[z] : 0;
+    return TTN_OK;
+}
+
 ttn_status ttn_set_tuning(ttn_ctx* c, int blocks, const unsigned char* variants) {
     if (!c) return fail(nullptr, TTN_E_INVALID, "ctx is NULL");
     if (blocks < 0 || blocks > TTN_MAX_CLUSTER || (blocks & (blocks - 1)) != 0)

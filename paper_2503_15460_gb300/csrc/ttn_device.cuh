@@ -493,7 +493,7 @@ __device__ void mode_prod_staged(T* out, const T* in, int64_t L, int n, int64_t 
 }
 
 template <class T, class TM>
-__device__ __noinline__ void mode_prod(T* out, const T* in, int64_t L, int nin, int nout, int64_t R, const T* M, bool transM,
+__device__ void mode_prod(T* out, const T* in, int64_t L, int nin, int nout, int64_t R, const T* M, bool transM,
                           double2 w, bool accumulate, const TM& tm) {
     count_flops_t<T>(8.0 * (double)(L * nout * R) * nin);
     if (transM || nin != nout) {
@@ -637,7 +637,7 @@ __device__ void heff_apply(T* out, const T* in, T* t1, T* t2, T* t3, const Shape
 // deals the tiles out to its blocks and adds the blocks' partials in rank
 // order.
 template <class T, class TM>
-__device__ __noinline__ void gram_acc(T* G, const T* X, const T* Y, const Shape& sh, int k, double2 w, const TM& tm) {
+__device__ void gram_acc(T* G, const T* X, const T* Y, const Shape& sh, int k, double2 w, const TM& tm) {
     constexpr int NT = TM::NT;
     const int chi = sh.d[k];
     const int64_t L = sh.before(k), R = sh.after(k), O = L * R;
@@ -1068,7 +1068,7 @@ __device__ void qr_mode_clu(T* A, const Shape& sh, int k, double2* Wc, double2* 
 }
 
 template <class T, class TM>
-__device__ __noinline__ void qr_mode(T* A, const Shape& sh, int k, double2* Wc, double2* Qc, double tol, Smem& sm, const TM& tm) {
+__device__ void qr_mode(T* A, const Shape& sh, int k, double2* Wc, double2* Qc, double tol, Smem& sm, const TM& tm) {
     if constexpr (TM::wide) qr_mode_clu(A, sh, k, Wc, Qc, tol, sm, tm);
     else qr_mode_solo(A, sh, k, Wc, Qc, tol, sm, tm);
 }
@@ -1092,7 +1092,7 @@ __device__ __forceinline__ double2 qr_R(const double2* Wc, int64_t m, int a, int
 // 8 nu term evaluations instead of 18 nu for 1-norm nu.  For a tridiagonal
 // H only the band is used, for an upper Hessenberg one only j >= i - 1.
 // ---------------------------------------------------------------------------
-__device__ __noinline__ void small_expm(Smem& sm, int m, double tau, bool band) {
+__device__ void small_expm(Smem& sm, int m, double tau, bool band) {
     if ((threadIdx.x >> 5) != 0) return;
     const int i = threadIdx.x & 31;
     double colsum = 0.0;

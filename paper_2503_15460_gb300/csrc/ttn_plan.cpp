@@ -30,6 +30,53 @@ namespace {
 
 int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
+// Minimum vertex cover of a bipartite graph (Konig's theorem): a maximum
+// matching by augmenting paths, then Z = the vertices reachable from the
+// unmatched left vertices along alternating paths (left to right on
+// non-matching edges, right to left on matching ones); the cover is
+// (L minus Z) together with (R in Z), its size that of the matching.
+// Returns the size and the cover's left part.
+size_t min_vertex_cover(const std::set<Key>& L, const std::set<Key>& R, const std::set<std::pair<Key, Key>>& E,
+                        std::set<Key>& cover_left) {
+    std::vector<Key> lv(L.begin(), L.end()), rv(R.begin(), R.end());
+    std::map<Key, int> li, ri;
+    for (size_t i = 0; i < lv.size(); ++i) li[lv[i]] = (int)i;
+    for (size_t i = 0; i < rv.size(); ++i) ri[rv[i]] = (int)i;
+    std::vector<std::vector<int>> adj(lv.size());
+    for (auto& e : E) adj[li[e.first]].push_back(ri[e.second]);
+    std::vector<int> ml(lv.size(), -1), mr(rv.size(), -1);
+    std::vector<char> seen;
+    std::function<bool(int)> augment = [&](int u) -> bool {
+        for (int v : adj[u]) {
+            if (seen[v]) continue;
+            seen[v] = 1;
+            if (mr[v] < 0 || augment(mr[v])) { ml[u] = v; mr[v] = u; return true; }
+        }
+        return false;
+    };
+    for (size_t u = 0; u < lv.size(); ++u) {
+        seen.assign(rv.size(), 0);
+        augment((int)u);
+    }
+    std::vector<char> zl(lv.size(), 0), zr(rv.size(), 0);
+    std::function<void(int)> walk = [&](int u) {
+        zl[u] = 1;
+        for (int v : adj[u]) {
+            if (zr[v] || ml[u] == v) continue;
+            zr[v] = 1;
+            if (mr[v] >= 0 && !zl[mr[v]]) walk(mr[v]);
+        }
+    };
+    for (size_t u = 0; u < lv.size(); ++u)
+        if (ml[u] < 0 && !zl[u]) walk((int)u);
+    size_t size = 0;
+    cover_left.clear();
+    for (size_t u = 0; u < lv.size(); ++u)
+        if (!zl[u]) { cover_left.insert(lv[u]); ++size; }
+    for (size_t v = 0; v < rv.size(); ++v) size += zr[v] ? 1 : 0;
+    return size;
+}
+
 // Smallest eigenvalue of a Hermitian d x d matrix (row-major) by cyclic
 // Jacobi rotations (Golub & Van Loan, Sec. 8.5, in the complex form that
 // first makes the pivot real).
@@ -215,8 +262,17 @@ struct Builder {
     // II.B.2 term (C)) or by their common inside factor (DNGRP: the down
     // channel is the sum of outside parts, term (B)), whichever gives fewer
     // channels.
-    enum { NONE = 0, UPGRP = 1, DNGRP = 2 };
+    // MIXED: the terms crossing the bond are assigned term by term from a
+    // minimum vertex cover of the bipartite graph whose vertices are their
+    // distinct inside parts and outside parts and whose edges are the terms
+    // (the hierarchical-SOP construction of Sec. II.B.2): a term whose inside
+    // part is in the cover is summed into that part's down channel, every
+    // other term into its outside part's up channel (whose vertex the cover
+    // then holds).  Used where this needs fewer channels than either uniform
+    // direction.
+    enum { NONE = 0, UPGRP = 1, DNGRP = 2, MIXED = 3 };
     std::vector<int> dir;
+    std::vector<std::set<Key>> dn_cover;          // MIXED bonds: inside parts in the cover
     std::vector<char> has_in, has_out;           // some term entirely inside / outside the subtree
     std::vector<int> up_loc, down_loc, phys_loc;
     std::vector<std::map<Key, int>> up_prod, down_prod, up_grp, down_grp, phys_grp;
@@ -265,6 +321,32 @@ struct Builder {
         return m;
     }
 
+    // Assignment of a term crossing bond c (its key restricted to both sides
+    // of the bond is non-empty): summed by its outside part (up group) or by
+    // its inside part (down group).
+    bool up_at(int c, const Key& key) const {
+        if (dir[c] == UPGRP) return true;
+        if (dir[c] != MIXED) return false;
+        return dn_cover[c].count(restrict_to(key, c, true)) == 0;
+    }
+    bool dn_at(int c, const Key& key) const {
+        if (dir[c] == DNGRP) return true;
+        if (dir[c] != MIXED) return false;
+        return dn_cover[c].count(restrict_to(key, c, true)) != 0;
+    }
+    // The up group of child bond ck for outside part E may stand for its
+    // members inside the up group being defined at bond c only if every one
+    // of its members belongs there too (true unless bond c is MIXED).
+    bool child_group_within(int ck, const Key& E, int c) const {
+        if (dir[c] != MIXED) return true;
+        for (const Key& key : h->terms) {
+            if (key.empty() || restrict_to(key, ck, true).empty() || restrict_to(key, ck, false) != E) continue;
+            if (!up_at(ck, key)) continue;
+            if (!up_at(c, key)) return false;
+        }
+        return true;
+    }
+
     // ---- channels (created on first use, defined by the closure loop) -----
     int chan(std::map<Key, int>& m, int kind, int c, const Key& key) {
         auto it = m.find(key);
@@ -301,7 +383,7 @@ struct Builder {
         for (size_t r = 0; r < h->terms.size(); ++r) {
             const Key& key = h->terms[r];
             Key in = restrict_to(key, l, true), out = restrict_to(key, l, false);
-            if (in.empty() || out != D) continue;
+            if (in.empty() || out != D || !up_at(l, key)) continue;
             for (int i = 0; i < d * d; ++i) sum[i] += h->coeff[r] * h->mats[in[0].second][i];
         }
         return phys_grp[l][D] = const_slot(d, d, sum);
@@ -348,14 +430,14 @@ struct Builder {
         };
         if (t.leaf(z)) {
             // modes {0 (physical), P}
-            if (dir[z] == UPGRP) {
+            if (up_at(z, key)) {
                 Key Dk = restrict_to(key, z, false);
                 sl[0] = get_phys_grp(z, Dk);
                 sl[P] = get_down_prod(z, Dk);
                 acc.add(true, sl, 1.0);
                 return;
             }
-            if (dir[z] == DNGRP) {
+            if (dn_at(z, key)) {
                 Key U = restrict_to(key, z, true);
                 sl[P] = get_down_grp(z, U);
                 sl[0] = get_phys_mat(z, U.at(0).second);
@@ -367,14 +449,14 @@ struct Builder {
             return;
         }
         for (int k : T) {
-            if (k == P || dir[t.ch[z][k]] != UPGRP) continue;
+            if (k == P || !up_at(t.ch[z][k], key)) continue;
             int c = t.ch[z][k];
             sl[k] = get_up_grp(c, restrict_to(key, c, false));
             fill_rest(k);
             acc.add(true, sl, 1.0);
             return;
         }
-        if (T.count(P) && z > 0 && dir[z] == DNGRP) {
+        if (T.count(P) && z > 0 && dn_at(z, key)) {
             sl[P] = get_down_grp(z, restrict_to(key, z, true));
             fill_rest(P);
             acc.add(true, sl, 1.0);
@@ -414,20 +496,23 @@ struct Builder {
                     for (int r = 0; r < R; ++r) {
                         const Key& key = h->terms[r];
                         Key in = restrict_to(key, c, true);
-                        if (in.empty() || restrict_to(key, c, false) != q.key) continue;
+                        if (in.empty() || restrict_to(key, c, false) != q.key || !up_at(c, key)) continue;
                         std::set<int> T = modes_of(c, in);
                         std::vector<int> s2(D, -1);
                         if (T.size() == 1) {
                             int k = *T.begin();
                             int ck = t.ch[c][k];
-                            if (dir[ck] == UPGRP) { s2[k] = get_up_grp(ck, q.key); acc.add(true, s2, 1.0); }
+                            if (up_at(ck, key) && child_group_within(ck, q.key, c)) { s2[k] = get_up_grp(ck, q.key); acc.add(true, s2, 1.0); }
                             else { s2[k] = get_up_prod(ck, in); acc.add(false, s2, h->coeff[r]); }
                             continue;
                         }
                         bool done = false;
                         for (int k : T) {
                             int ck = t.ch[c][k];
-                            if (dir[ck] != UPGRP) continue;
+                            if (!up_at(ck, key)) continue;
+                            // the first child where the term is grouped; its group only
+                            // if all of the group's members belong to this channel
+                            if (!child_group_within(ck, restrict_to(key, ck, false), c)) break;
                             s2[k] = get_up_grp(ck, restrict_to(key, ck, false));
                             for (int j : T) if (j != k) s2[j] = get_up_prod(t.ch[c][j], restrict_mode(c, in, j));
                             acc.add(true, s2, 1.0);
@@ -470,24 +555,24 @@ struct Builder {
             for (int r = 0; r < R; ++r) {
                 const Key& key = h->terms[r];
                 Key out = restrict_to(key, c, false);
-                if (out.empty() || restrict_to(key, c, true) != q.key) continue;
+                if (out.empty() || restrict_to(key, c, true) != q.key || !dn_at(c, key)) continue;
                 std::set<int> T = modes_of(z, out);
                 std::vector<int> s2(D, -1);
                 if (T.size() == 1) {
                     int j = *T.begin();
                     if (j == P) {
-                        if (z > 0 && dir[z] == DNGRP) { s2[P] = get_down_grp(z, q.key); acc.add(true, s2, 1.0); }
+                        if (z > 0 && dn_at(z, key)) { s2[P] = get_down_grp(z, q.key); acc.add(true, s2, 1.0); }
                         else { s2[P] = get_down_prod(z, out); acc.add(false, s2, h->coeff[r]); }
                     } else {
                         int cj = t.ch[z][j];
-                        if (dir[cj] == UPGRP) { s2[j] = get_up_grp(cj, q.key); acc.add(true, s2, 1.0); }
+                        if (up_at(cj, key)) { s2[j] = get_up_grp(cj, q.key); acc.add(true, s2, 1.0); }
                         else { s2[j] = get_up_prod(cj, out); acc.add(false, s2, h->coeff[r]); }
                     }
                     continue;
                 }
                 bool done = false;
                 for (int j : T) {
-                    if (j == P || dir[t.ch[z][j]] != UPGRP) continue;
+                    if (j == P || !up_at(t.ch[z][j], key)) continue;
                     int cj = t.ch[z][j];
                     s2[j] = get_up_grp(cj, restrict_to(key, cj, false));
                     for (int i : T) if (i != j) { Key part = restrict_mode(z, out, i); s2[i] = (i == P) ? get_down_prod(z, part) : get_up_prod(t.ch[z][i], part); }
@@ -495,7 +580,7 @@ struct Builder {
                     done = true;
                     break;
                 }
-                if (!done && T.count(P) && z > 0 && dir[z] == DNGRP) {
+                if (!done && T.count(P) && z > 0 && dn_at(z, key)) {
                     s2[P] = get_down_grp(z, restrict_to(key, z, true));
                     for (int i : T) if (i != P) s2[i] = get_up_prod(t.ch[z][i], restrict_mode(z, out, i));
                     acc.add(true, s2, 1.0);
@@ -548,17 +633,27 @@ struct Builder {
             }
             phys_loc[l] = const_slot(t.phys[l], t.phys[l], loc_sum[l]);
         }
+        dn_cover.assign(n, {});
         for (int c = 1; c < n; ++c) {
             std::set<Key> ins, outs;
+            std::set<std::pair<Key, Key>> edges;
             for (int r = 0; r < R; ++r) {
                 const Key& key = h->terms[r];
                 if (key.empty()) continue;
                 Key in = restrict_to(key, c, true), out = restrict_to(key, c, false);
                 if (!in.empty() && out.empty()) has_in[c] = 1;
                 else if (in.empty() && !out.empty()) has_out[c] = 1;
-                else { ins.insert(in); outs.insert(out); }
+                else { ins.insert(in); outs.insert(out); edges.insert({in, out}); }
             }
-            if (!ins.empty()) dir[c] = outs.size() <= ins.size() ? UPGRP : DNGRP;
+            if (ins.empty()) continue;
+            std::set<Key> cov_in;
+            const size_t mvc = min_vertex_cover(ins, outs, edges, cov_in);
+            if (mvc < std::min(ins.size(), outs.size())) {
+                dir[c] = MIXED;
+                dn_cover[c] = cov_in;
+            } else {
+                dir[c] = outs.size() <= ins.size() ? UPGRP : DNGRP;
+            }
         }
     }
 
@@ -592,8 +687,8 @@ struct Builder {
             if (key.empty()) { acc.add(false, {-1, -1}, h->coeff[r]); continue; }
             Key in = restrict_to(key, c, true), out = restrict_to(key, c, false);
             if (in.empty() || out.empty()) continue;
-            if (dir[c] == UPGRP) acc.add(true, {get_up_grp(c, out), get_down_prod(c, out)}, 1.0);
-            else if (dir[c] == DNGRP) acc.add(true, {get_up_prod(c, in), get_down_grp(c, in)}, 1.0);
+            if (up_at(c, key)) acc.add(true, {get_up_grp(c, out), get_down_prod(c, out)}, 1.0);
+            else if (dn_at(c, key)) acc.add(true, {get_up_prod(c, in), get_down_grp(c, in)}, 1.0);
             else acc.add(false, {get_up_prod(c, in), get_down_prod(c, out)}, h->coeff[r]);
         }
         return acc.out(-1);
@@ -697,6 +792,7 @@ struct Builder {
         bond_raw_rng.assign(n, {0, 0});
         down_rng.assign(n, {});
         std::vector<std::vector<Proto>> heff(n), bond(n);
+        p.op_bond_dim.assign(n, 0);
         for (int z = 0; z < n; ++z) {
             heff[z] = heff_terms(z);
             if (z > 0) bond[z] = bond_terms(z);
@@ -713,6 +809,7 @@ struct Builder {
                 for (auto& rd : br) bond_combo[z].push_back(push_entries(rd));
                 bond_rng[z] = push_entries(bs);
                 bond_raw_rng[z] = push_entries(bond[z]);
+                p.op_bond_dim[z] = (int)bond[z].size();
                 up_rng[z] = push_entries(up_entries[z]);
             }
         }

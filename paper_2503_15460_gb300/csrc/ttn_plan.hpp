@@ -75,6 +75,9 @@ struct Plan {
     // reported with e_shift added.  Zero in complex128 and for generators
     // that are not Hermitian.
     double e_shift = 0.0;
+    // Channels crossing each bond (entries of the bond operator: pairs of
+    // single-particle and mean-field operators), index = child node.
+    std::vector<int> op_bond_dim;
     int max_stamps = 0;
     int64_t total_bytes = 0;
     int max_chi = 1;

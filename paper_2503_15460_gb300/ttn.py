@@ -78,6 +78,7 @@ _sig = {
     "ttn_pipe_peaks": ([_P, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
     "ttn_autotune": ([_P, C.c_double, C.c_int, C.c_int, C.POINTER(C.c_double)], C.c_int),
     "ttn_set_tuning": ([_P, C.c_int, np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")], C.c_int),
+    "ttn_operator_dims": ([_P, _I32], C.c_int),
     "ttn_tuning": ([_P, C.POINTER(C.c_int), np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS"),
                     C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int)], C.c_int),
     "ttn_mode_product_c64": ([_P, C.c_int64, C.c_int, C.c_int64, _P, _P, _P, C.c_double, C.c_double, C.c_int,
@@ -355,6 +356,12 @@ def ttn_tuning(ctx):
             "default_ms": d.value, "trials": n.value}
 
 
+def ttn_operator_dims(ctx, n_nodes):
+    out = np.zeros(n_nodes, dtype=np.int32)
+    _check(_lib.ttn_operator_dims(ctx, out), ctx)
+    return out
+
+
 def ttn_set_tuning(ctx, blocks, variants):
     v = np.zeros(65, dtype=np.uint8)
     for n, x in (variants.items() if isinstance(variants, dict) else enumerate(variants)):
@@ -566,6 +573,10 @@ class Context:
 
     def tuning(self):
         return ttn_tuning(self.h)
+
+    def operator_dims(self):
+        """Channels of the hierarchical SOP crossing each bond (index = child)."""
+        return ttn_operator_dims(self.h, self.tree.n)
 
     def set_tuning(self, blocks, variants):
         ttn_set_tuning(self.h, blocks, variants)

@@ -107,7 +107,7 @@ def _largest_growth(gpu_lib, p, nsteps, eps, chi_max, precision):
 
 def _oracle_floor(p, nsteps, eps, chi_max):
     """The oracle's own response to 1e-15 perturbations of the initial
-    tensors (two seeds): with 25 functions entering unoccupied at once, the
+    tensors (two seeds): with many functions entering unoccupied at once, the
     one-site dynamics of the unoccupied directions is set by rounding, so no
     implementation can agree with the oracle better than this."""
     def run(pert, seed):
@@ -128,6 +128,11 @@ def many_channel_floor():
     return _oracle_floor(many_channel_problem(), 3, 1e-6, 32)
 
 
+@pytest.fixture(scope="module")
+def many_channel_floor_mixed():
+    return _oracle_floor(many_channel_problem(), 3, 3e-5, 32)
+
+
 def test_expansion_growth_above_16_fp64(gpu_lib, many_channel_floor):
     """Identical bond trajectories (one growth adds more than 16 functions);
     populations within 20 x the oracle's rounding floor on this case
@@ -137,12 +142,16 @@ def test_expansion_growth_above_16_fp64(gpu_lib, many_channel_floor):
     assert worst <= max(1e-10, 20.0 * many_channel_floor)
 
 
-def test_expansion_growth_above_16_mixed(gpu_lib):
+def test_expansion_growth_above_16_mixed(gpu_lib, many_channel_floor_mixed):
     """Complex64 contractions resolve eigenvalues of the spawning operator
     down to about 1e-6 of the largest; at eps 3e-5 the growth of 17 functions
     has its smallest accepted eigenvalue at 3.2e-6 of the largest and its
     first rejected one 8 % below the threshold in sigma, so the decisions
-    are clear of both the threshold and the complex64 floor."""
+    are clear of both the threshold and the complex64 floor and the bond
+    trajectory is the oracle's.  Populations: the new functions enter
+    unoccupied, so (as for complex128) the bar is 20 x the oracle's own
+    response to 1e-15 perturbations (3e-8 .. 1.3e-7 here), never below the
+    mixed form's 1e-6."""
     jump, worst = _largest_growth(gpu_lib, many_channel_problem(), 3, 3e-5, 32, gpu_lib.TTN_MIXED)
     assert jump > 16
-    assert worst <= 1e-6
+    assert worst <= max(1e-6, 20.0 * many_channel_floor_mixed)
