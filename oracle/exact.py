@@ -60,3 +60,22 @@ def leaf_populations(tree, psi: np.ndarray, leaves):
         rho = leaf_reduced_density(psi, dims, all_leaves.index(l))
         out.append(np.real(np.diag(rho)) / np.real(np.trace(rho)))
     return out
+
+
+def full_multiset_hamiltonian(tree, H, dense: bool = False):
+    """sum_r c_r |a_r><b_r| (x) kron_{leaves} (factor or identity) for a
+    workloads.MultiSetSOP: the set index is the slowest index."""
+    leaves = tree.leaves()
+    dims = [int(tree.phys_dim[l]) for l in leaves]
+    D = int(np.prod(dims))
+    S = int(H.n_sets)
+    out = sp.csr_matrix((S * D, S * D), dtype=np.complex128)
+    for c, fs, a, b in zip(H.coeffs, H.factors, H.bra, H.ket):
+        fac = {l: H.mats[m] for (l, m) in fs}
+        E = sp.csr_matrix(([1.0], ([int(a)], [int(b)])), shape=(S, S), dtype=np.complex128)
+        M = E
+        for l, d in zip(leaves, dims):
+            X = sp.csr_matrix(fac[l]) if l in fac else sp.identity(d, dtype=np.complex128, format="csr")
+            M = sp.kron(M, X, format="csr")
+        out = out + c * M
+    return out.toarray() if dense else out

@@ -32,7 +32,8 @@ __all__ = [
     "discretise_uniform_density", "spin_boson_sop", "vibronic_sop",
     "drude_lorentz_exponentials", "heom_sop",
     "config_c1", "config_c2", "config_c3", "config_c4", "config_c5_requests",
-    "Problem",
+    "Problem", "MultiSetSOP", "MultiSetProblem", "multiset_product_state",
+    "multiset_vibronic_problem",
 ]
 
 
@@ -214,6 +215,36 @@ class SOP:
                 np.ascontiguousarray(flat), np.array(off, dtype=np.int64))
 
 
+@dataclass
+class MultiSetSOP(SOP):
+    """Multi-set Hamiltonian (paper Sec. II.A, multi-set ansatz)
+    H = sum_r coeffs[r] |bra[r]><ket[r]| (x) prod_{(leaf, m) in factors[r]} mats[m]:
+    the set index (the system state alpha) is not a leaf of the tree; every
+    term names the pair of set states it connects and a product of leaf
+    factors acting on the environment degrees of freedom (an empty product
+    is the identity there)."""
+    n_sets: int = 1
+    bra: list = field(default_factory=list)
+    ket: list = field(default_factory=list)
+
+    def add(self, c, *pairs):
+        raise TypeError("multi-set terms name their set pair: use add_set(alpha, beta, c, ...)")
+
+    def add_set(self, alpha, beta, c, *pairs):
+        """Add c |alpha><beta| (x) prod (leaf, matrix).  Zero coefficients are dropped."""
+        assert 0 <= alpha < self.n_sets and 0 <= beta < self.n_sets
+        if c == 0:
+            return
+        self.coeffs.append(complex(c))
+        self.factors.append([(int(l), self.mat_id(M)) for (l, M) in pairs])
+        self.bra.append(int(alpha))
+        self.ket.append(int(beta))
+
+    def to_csr(self):
+        """The single-set flat arrays plus the per-term set pair."""
+        return super().to_csr() + (np.array(self.bra, dtype=np.int32), np.array(self.ket, dtype=np.int32))
+
+
 # ----------------------------------------------------------------------------
 # Initial states
 # ----------------------------------------------------------------------------
@@ -265,6 +296,20 @@ def product_state(t: Tree, leaf_vecs: dict) -> list:
                 M[i, i] = 1.0
             A.append(M.reshape(dims))
     return [np.ascontiguousarray(a.reshape(t.mode_dims(z))) for z, a in enumerate(A)]
+
+
+def multiset_product_state(t: Tree, amps, leaf_vecs=None) -> list:
+    """Per-set tensor lists of sum_alpha amps[alpha] |alpha> prod_leaf |v_leaf^alpha>:
+    every set is ``product_state`` of its own leaf vectors (``leaf_vecs[alpha]``,
+    default the basis vector e_0 on every leaf) with its root tensor scaled by
+    amps[alpha] (``leaf_vecs`` indexed by alpha; zero amplitudes allowed: an unoccupied set keeps orthonormal
+    single-particle functions and a zero top tensor)."""
+    out = []
+    for a, amp in enumerate(amps):
+        A = product_state(t, {} if leaf_vecs is None else leaf_vecs[a])
+        A[0] = A[0] * complex(amp)
+        out.append(A)
+    return out
 
 
 # ----------------------------------------------------------------------------
@@ -586,6 +631,64 @@ def vibronic_balanced_problem(n_modes: int, d: int, chi: int, seed: int, dt: flo
     A = product_state(t, {el: v})
     return Problem(f"vibronic_2x{n_modes}_d{d}_chi{chi}_seed{seed}", t, H, A, dt, nsteps, [el] + modes,
                    {"el": el, "modes": modes, "d_modes": d_modes})
+
+
+@dataclass
+class MultiSetProblem:
+    name: str
+    tree: Tree               # the environment tree (shared by every set)
+    H: MultiSetSOP
+    tensors: list            # tensors[alpha][z], centre at the root of every set
+    dt: float
+    nsteps: int
+    meta: dict = field(default_factory=dict)
+
+
+def multiset_vibronic_problem(n_states: int = 3, n_modes: int = 6, d: int = 6, chi: int = 4,
+                              seed: int = 7, dt: float = 0.1, nsteps: int = 50,
+                              n_coupling_modes: int = 2) -> MultiSetProblem:
+    """Linear vibronic coupling model in the multi-set form (the electronic
+    states are the sets, the modes the environment tree; the form of the
+    exciton models of paper Sec. IV.B), seeded:
+      H^{ss}   = E_s + sum_i w_i (n_i + 1/2) + sum_i kappa_i^s Q_i
+      H^{ss'}  = J_{ss'} + sum_{i in coupling modes} lam_i^{ss'} Q_i   (s != s', symmetric)
+    with w ~ U[0.05, 0.5], E_s ~ N(0, 0.05^2), kappa ~ N(0, 0.05^2),
+    J ~ N(0, 0.03^2), lam ~ N(0, 0.03^2), Q = (a + a^+)/sqrt(2), on a balanced
+    binary tree over the modes (leaf bonds min(chi, d), interior bonds chi).
+    Initial state: set 0 times the vibrational vacuum, the other sets empty."""
+    rng = np.random.default_rng(seed)
+    omega = rng.uniform(0.05, 0.5, n_modes)
+    E = rng.normal(0.0, 0.05, n_states)
+    kappa = rng.normal(0.0, 0.05, (n_modes, n_states))
+    cm = np.sort(rng.choice(n_modes, min(n_coupling_modes, n_modes), replace=False))
+    J = rng.normal(0.0, 0.03, (n_states, n_states))
+    lam = rng.normal(0.0, 0.03, (len(cm), n_states, n_states))
+    leaves = [("leaf", d, min(chi, d), f"m{k}") for k in range(n_modes)]
+    spec = balanced_spec(leaves, chi)
+    if spec[0] == "leaf":
+        spec = ("node", 1, [spec])
+    t = build_tree(spec)
+    modes = [t.leaf_of_label(f"m{i}") for i in range(n_modes)]
+    B = boson_ops(d)
+    Q = B["x"] / np.sqrt(2.0)
+    num = B["n"] + 0.5 * np.eye(d)
+    H = MultiSetSOP(hermitian=True, n_sets=n_states)
+    for s_ in range(n_states):
+        H.add_set(s_, s_, E[s_])
+        for i, leaf in enumerate(modes):
+            H.add_set(s_, s_, omega[i], (leaf, num))
+            H.add_set(s_, s_, kappa[i, s_], (leaf, Q))
+    for s_ in range(n_states):
+        for s2 in range(n_states):
+            if s2 == s_:
+                continue
+            a, b = min(s_, s2), max(s_, s2)
+            H.add_set(s_, s2, J[a, b])
+            for j, i in enumerate(cm):
+                H.add_set(s_, s2, lam[j, a, b], (modes[i], Q))
+    A = multiset_product_state(t, [1.0] + [0.0] * (n_states - 1))
+    return MultiSetProblem(f"multiset_vibronic_{n_states}x{n_modes}_d{d}_chi{chi}_seed{seed}", t, H, A,
+                           dt, nsteps, {"modes": modes, "coupling_modes": cm})
 
 
 def c5_problem(req: dict) -> Problem:
