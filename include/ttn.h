@@ -188,6 +188,51 @@ ttn_status ttn_set_sop_hamiltonian(ttn_ctx* ctx, int n_terms, const ttn_c128* co
  * smooth c(t).  The cost is one host re-plan and one environment build. */
 ttn_status ttn_set_coefficients(ttn_ctx* ctx, int n_terms, const ttn_c128* coeff);
 
+/* Multi-set states (Sec. II.A, multi-set ansatz): |Psi> = sum_alpha |alpha>
+ * |Psi^alpha> with one TTN per set state alpha (the system state, e.g. an
+ * electronic state), all on the context's tree with the same bond
+ * dimensions.  The operator is
+ *     H = sum_r c_r |bra[r]><ket[r]| (x) prod_{factors of r} M_f
+ * given like ttn_set_sop_hamiltonian plus, per term, the set pair
+ * bra[r], ket[r] in 0 .. n_sets-1 (1 <= n_sets <= 64).  Every step is the
+ * single-set projector-splitting step with all sets' tensors of a node (or
+ * bond) propagated together, cross-set environments between the sets'
+ * functions (an operator that is the identity on a subtree becomes the
+ * overlap of the two sets' functions there when bra != ket), and QR gauge
+ * moves done set by set.  A single-set state becomes multi-set here: set 0
+ * keeps it, every other set starts empty (set 0's isometries, zero top
+ * tensor).  A state with another set count > 1 gives TTN_E_INVALID.
+ * ttn_set_coefficients replays the set pairs.  Multi-set contexts support
+ * ttn_step (no subspace expansion: the paper leaves it open for this
+ * ansatz), ttn_step_batch, the request server, ttn_norm_energy (whole
+ * state), ttn_set_populations and the state calls below; the single-set
+ * state, density, vacuum-projection, ground-state and checkpoint calls
+ * return TTN_E_INVALID. */
+ttn_status ttn_set_multiset_hamiltonian(ttn_ctx* ctx, int n_sets, int n_terms, const ttn_c128* coeff,
+                                        const int* term_ptr, const int* factor_leaf,
+                                        const ttn_c128* factor_mats, const int64_t* factor_mat_off,
+                                        const int* bra, const int* ket, int hermitian);
+
+/* Set every set's node tensors (after ttn_set_multiset_hamiltonian; n_sets
+ * must equal its set count).  The tensor of set alpha, node z is
+ * tensors[offsets[alpha*n_nodes + z] .. offsets[alpha*n_nodes + z + 1]);
+ * offsets has n_sets*n_nodes+1 entries.  Each set in canonical gauge with
+ * its centre at the root (non-root tensors isometric; a set may be empty:
+ * zero top tensor).  Environments are rebuilt. */
+ttn_status ttn_set_multiset_state(ttn_ctx* ctx, int n_sets, const ttn_c128* tensors, const int64_t* offsets);
+
+/* Copy set alpha's node tensors to the host in the layout of ttn_get_state. */
+ttn_status ttn_get_multiset_state(ttn_ctx* ctx, int alpha, ttn_c128* tensors, int64_t* offsets);
+
+/* Populations <Psi^alpha|Psi^alpha> of every set (the squared norm of each
+ * set's top tensor, the centre being at the root between steps), computed
+ * on the device; pops has n_sets entries (a single-set context gives its
+ * squared norm). */
+ttn_status ttn_set_populations(ttn_ctx* ctx, double* pops);
+
+/* Set count of the context's state (1 for a single-set state). */
+ttn_status ttn_n_sets(const ttn_ctx* ctx, int* n_sets);
+
 /* Checkpoint / resume (the paper has no counterpart: long propagations
  * are resumed from saved states).  ttn_save writes the tree (with the
  * current bond dimensions, which subspace expansion may have grown), the
@@ -325,7 +370,11 @@ ttn_status ttn_set_device(int device);
  *      the register-fibre product (n <= 32 complex64 / 16 complex128) or
  *      the shared-memory-staged one;
  *   4  with 2, in TTN_MIXED also the tcgen05 tensor-core product (3xTF32)
- *      for n <= 48.
+ *      for n <= 48.  Contexts with such a dimension launch a separate
+ *      build of the sweep kernel that carries the tcgen05 code (the default
+ *      build has none: it keeps two blocks per SM overlapping); the request
+ *      server always runs the default build, where those dimensions take
+ *      the staged routine.
  * tuned_ms (may be NULL) receives the time of `steps` steps with the chosen
  * configuration.  The choice changes results only through rounding.
  * Errors: TTN_E_INVALID (steps outside 1..1000), TTN_E_STATE (no
@@ -348,7 +397,10 @@ ttn_status ttn_tuning(const ttn_ctx* ctx, int* blocks, unsigned char* variants, 
  * on both sides, the size of a minimum vertex cover of the bipartite graph
  * whose vertices are their distinct inside and outside parts (a term is
  * summed into the channel of its inside part when that is in the cover,
- * else into the channel of its outside part); out[0] = 0.  Works on
+ * else into the channel of its outside part); out[0] = 0.  For a multi-set
+ * operator (ttn_set_multiset_hamiltonian): the number of distinct
+ * (bra set, ket set, inside part) plus (bra set, ket set, outside part)
+ * channels, less the same-set empty ones (identities).  Works on
  * host-resident contexts (no device work).  TTN_E_STATE without a
  * Hamiltonian. */
 ttn_status ttn_operator_dims(const ttn_ctx* ctx, int* out);

@@ -92,6 +92,13 @@ TtnInstance ttn::make_instance(ttn_ctx* c, const DevProgram& p) {
 
 ttn_status ttn::ctx_fail(ttn_ctx* c, ttn_status s, const std::string& msg) { return fail(c, s, msg); }
 
+bool ttn::ctx_uses_tc(const ttn_ctx* c) {
+    if (c->precision != TTN_MIXED) return false;
+    for (int n = 0; n <= TTN_MAXCHI; ++n)
+        if (c->mp_variant[n] == 2) return true;
+    return false;
+}
+
 int ttn::ctx_cluster(const ttn_ctx* c) {
     const int need = c->plan.max_chi > kSoloMaxDim ? 2 : 1;
     if (c->cluster_req > 0) return std::max(c->cluster_req, need);
@@ -135,7 +142,7 @@ OpsLayout ops_layout(const ttn::Plan& P) {
     for (auto& s : P.slots) L.slot_bytes = std::max(L.slot_bytes, (size_t)s.off + (size_t)s.rows * s.cols * P.esz);
     L.slot_bytes = al(L.slot_bytes);
     size_t n_ops_total = P.init_prog.ops.size() + P.step_prog.ops.size() + P.norm_energy_prog.ops.size() +
-                         P.spawn_prog.ops.size() + P.ground_prog.ops.size();
+                         P.spawn_prog.ops.size() + P.ground_prog.ops.size() + P.setpop_prog.ops.size();
     for (auto& p : P.rdm_prog) n_ops_total += p.ops.size();
     for (auto& p : P.vac_prog) n_ops_total += p.ops.size();
     for (auto& p : P.to_root_prog) n_ops_total += p.ops.size();
@@ -161,7 +168,8 @@ ttn_status run_program(ttn_ctx* c, const DevProgram& p, double dt, int nrep) {
     if (p.n_ops == 0 || nrep == 0) return TTN_OK;
     TtnInstance in = make_instance(c, p);
     CK(cudaMemcpyAsync(c->d_inst, &in, sizeof(in), cudaMemcpyHostToDevice, c->stream), "instance upload");
-    int e = ttn_launch_program(c->precision, ttn::ctx_cluster(c), c->d_inst, 1, dt, nrep, c->stream);
+    int e = ttn_launch_program(c->precision, ttn::ctx_cluster(c), c->d_inst, 1, dt, nrep, c->stream,
+                               ttn::ctx_uses_tc(c));
     if (e != 0) return cuda_fail(c, (cudaError_t)e, "kernel launch");
     return check_status(c);
 }
@@ -187,7 +195,7 @@ void free_ops(ttn_ctx* c) {
     c->ops_bytes = 0;
     c->d_slots = nullptr;
     c->d_entries = nullptr;
-    c->init_p = c->step_p = c->ne_p = c->spawn_p = c->ground_p = DevProgram();
+    c->init_p = c->step_p = c->ne_p = c->spawn_p = c->ground_p = c->setpop_p = DevProgram();
     c->rdm_p.clear(); c->vac_p.clear(); c->to_root_p.clear();
     c->d_inst = nullptr;
 }
@@ -236,6 +244,7 @@ ttn_status upload_ops(ttn_ctx* c) {
             o.b = s.b_off >= 0 ? (void*)(c->d_state + s.b_off) : nullptr;
             o.out = s.out_off >= 0 ? (double*)(c->d_state + s.out_off) : nullptr;
             if (o.type == TTN_OP_SPAWN) o.c = o.b;      // the child tensor
+            else o.c = s.c_off >= 0 ? (void*)(c->d_state + s.c_off) : nullptr;   // ENV: ket tensor
             std::memcpy(host.data() + cur, &o, sizeof(TtnOp));
             cur += sizeof(TtnOp);
         }
@@ -246,6 +255,7 @@ ttn_status upload_ops(ttn_ctx* c) {
     c->ne_p = link(P.norm_energy_prog);
     c->spawn_p = link(P.spawn_prog);
     c->ground_p = link(P.ground_prog);
+    c->setpop_p = link(P.setpop_prog);
     for (auto& p : P.rdm_prog) c->rdm_p.push_back(link(p));
     for (auto& p : P.vac_prog) c->vac_p.push_back(link(p));
     for (auto& p : P.to_root_prog) c->to_root_p.push_back(link(p));
@@ -267,7 +277,7 @@ ttn_status download_state(ttn_ctx* c, std::vector<std::vector<cplx>>& A) {
     A.assign(c->tree.n, {});
     for (int u = 0; u < c->tree.n; ++u) {
         const cplx* src = (const cplx*)(raw.data() + c->plan.tensor_off[u]);
-        A[u].assign(src, src + c->tree.size[u]);
+        A[u].assign(src, src + c->plan.nset * c->tree.size[u]);     // all set blocks
     }
     return TTN_OK;
 }
@@ -330,12 +340,15 @@ ttn_status grow_bond(ttn_ctx* c, int child, int p, const std::vector<cplx>& U) {
 
 // One expansion pass: run the spawn program until it finishes without a hit.
 ttn_status expand_pass(ttn_ctx* c, double dt, double eps, int chi_max) {
+    if (c->plan.nset > 1)
+        return fail(c, TTN_E_INVALID, "subspace expansion is for single-set states (the paper leaves the multi-set case open)");
     for (int guard = 0; guard < 100000; ++guard) {
         if (c->spawn_p.n_ops == 0) return TTN_OK;
         TtnInstance in = make_instance(c, c->spawn_p);
         in.chi_max = chi_max; in.spawn_eps = eps; in.spawn_dt = dt;
         CK(cudaMemcpyAsync(c->d_inst, &in, sizeof(in), cudaMemcpyHostToDevice, c->stream), "instance upload");
-        int e = ttn_launch_program(c->precision, ttn::ctx_cluster(c), c->d_inst, 1, dt, 1, c->stream);
+        int e = ttn_launch_program(c->precision, ttn::ctx_cluster(c), c->d_inst, 1, dt, 1, c->stream,
+                                   ttn::ctx_uses_tc(c));
         if (e != 0) return cuda_fail(c, (cudaError_t)e, "kernel launch");
         bool hit = false;
         ttn_status s = check_status_spawn(c, &hit);
@@ -563,6 +576,7 @@ ttn_status ttn_footprint(const ttn_ctx* c, size_t* bytes) {
 
 ttn_status ttn_set_state(ttn_ctx* c, const ttn_c128* tensors, const int64_t* offsets) {
     ttn_status u = usable(c); if (u) return u;
+    if (c->plan.nset > 1) return fail(c, TTN_E_INVALID, "the state is multi-set: use ttn_set_multiset_state");
     if (!tensors || !offsets) return fail(c, TTN_E_INVALID, "null tensors / offsets");
     std::vector<std::vector<cplx>> A(c->tree.n);
     for (int z = 0; z < c->tree.n; ++z) {
@@ -578,6 +592,7 @@ ttn_status ttn_set_state(ttn_ctx* c, const ttn_c128* tensors, const int64_t* off
 
 ttn_status ttn_set_product_state(ttn_ctx* c, const ttn_c128* leaf_vecs, const int64_t* leaf_offsets) {
     ttn_status u = usable(c); if (u) return u;
+    if (c->plan.nset > 1) return fail(c, TTN_E_INVALID, "the state is multi-set: use ttn_set_multiset_state");
     if (!leaf_vecs || !leaf_offsets) return fail(c, TTN_E_INVALID, "null leaf vectors");
     std::vector<std::vector<cplx>> vecs(c->tree.n), A;
     for (int z = 0; z < c->tree.n; ++z) {
@@ -592,19 +607,46 @@ ttn_status ttn_set_product_state(ttn_ctx* c, const ttn_c128* leaf_vecs, const in
     return take_state(c, A);
 }
 
-ttn_status ttn_set_sop_hamiltonian(ttn_ctx* c, int n_terms, const ttn_c128* coeff, const int* term_ptr,
-                                   const int* factor_leaf, const ttn_c128* factor_mats,
-                                   const int64_t* factor_mat_off, int hermitian) {
+// Shared by the single- and multi-set Hamiltonian setters.  A Hamiltonian
+// with another set count than the state's converts a single-set state into
+// a multi-set one: set 0 is the old state, every other set starts empty
+// (copies of set 0's isometries with a zero top tensor).
+static ttn_status set_ham(ttn_ctx* c, int n_sets, int n_terms, const ttn_c128* coeff, const int* term_ptr,
+                          const int* factor_leaf, const ttn_c128* factor_mats, const int64_t* factor_mat_off,
+                          const int* bra, const int* ket, int hermitian) {
     ttn_status u = usable(c); if (u) return u;
     if (n_terms > 0 && term_ptr && term_ptr[n_terms] > 0 && (!factor_leaf || !factor_mats || !factor_mat_off))
         return fail(c, TTN_E_INVALID, "null factor arrays");
     ttn::Hamiltonian h;
     std::string msg = ttn::build_hamiltonian(c->tree, n_terms, (const cplx*)coeff, term_ptr, factor_leaf,
-                                             (const cplx*)factor_mats, factor_mat_off, hermitian, h);
+                                             (const cplx*)factor_mats, factor_mat_off, hermitian, h, n_sets, bra,
+                                             ket);
     if (!msg.empty()) return fail(c, TTN_E_INVALID, msg);
+    const int old_sets = c->plan.nset;
+    if (old_sets != n_sets && old_sets != 1)
+        return fail(c, TTN_E_INVALID, "the state has " + std::to_string(old_sets) + " sets, the operator " +
+                    std::to_string(n_sets));
     ttn::Plan P;
     msg = ttn::make_plan(c->tree, &h, c->precision, P);
     if (!msg.empty()) return fail(c, TTN_E_INVALID, msg);
+    // a single-set state becoming multi-set
+    std::vector<std::vector<cplx>> A;
+    const bool convert = old_sets != n_sets;
+    if (convert) {
+        if (c->resident) {
+            ttn_status s = download_state(c, A);
+            if (s) return s;
+        } else {
+            A = c->host_A;
+        }
+        for (int z = 0; z < c->tree.n; ++z) {
+            const int64_t sz = c->tree.size[z];
+            std::vector<cplx> blk(A[z].begin(), A[z].begin() + sz);
+            A[z].resize((size_t)n_sets * sz);
+            for (int a = 1; a < n_sets; ++a)
+                for (int64_t i = 0; i < sz; ++i) A[z][a * sz + i] = z == 0 ? cplx(0.0) : blk[i];
+        }
+    }
     {
         const int nf = n_terms > 0 && term_ptr ? term_ptr[n_terms] : 0;
         int64_t nm = 0;
@@ -620,14 +662,26 @@ ttn_status ttn_set_sop_hamiltonian(ttn_ctx* c, int n_terms, const ttn_c128* coef
         c->sop_coeff.swap(sc); c->sop_ptr.swap(sp); c->sop_leaf.swap(sl);
         c->sop_mats.swap(sm_); c->sop_off.swap(so);
         c->sop_herm = hermitian;
+        c->sop_nsets = n_sets;
+        c->sop_bra.assign(bra && n_sets > 1 ? bra : nullptr, bra && n_sets > 1 ? bra + n_terms : nullptr);
+        c->sop_ket.assign(ket && n_sets > 1 ? ket : nullptr, ket && n_sets > 1 ? ket + n_terms : nullptr);
     }
     if (!c->resident) {
         c->ham = h;
         c->has_h = true;
         c->plan = P;
+        if (convert) c->host_A.swap(A);
         return TTN_OK;
     }
-    if ((size_t)P.total_bytes > c->state_bytes) {
+    if (convert) {
+        char* fresh = nullptr;
+        cudaError_t ae = dev_alloc(c, &fresh, P.total_bytes);
+        if (ae != cudaSuccess) return alloc_fail(c, ae, "device allocation (state)");
+        dev_free(c, c->d_state);
+        c->d_state = fresh;
+        c->state_bytes = P.total_bytes;
+        CK(cudaMemsetAsync(c->d_state, 0, c->state_bytes, c->stream), "memset");
+    } else if ((size_t)P.total_bytes > c->state_bytes) {
         char* fresh = nullptr;
         cudaError_t ae = dev_alloc(c, &fresh, P.total_bytes);
         if (ae != cudaSuccess) return alloc_fail(c, ae, "device allocation (state)");
@@ -643,11 +697,105 @@ ttn_status ttn_set_sop_hamiltonian(ttn_ctx* c, int n_terms, const ttn_c128* coef
     c->plan = P;
     ttn_status s = upload_ops(c);
     if (s) { c->failed = true; return s; }
+    if (convert) {
+        s = upload_state(c, A);
+        if (s) { c->failed = true; return s; }
+    }
     return run_program(c, c->init_p, 0.0, 1);
+}
+
+ttn_status ttn_set_sop_hamiltonian(ttn_ctx* c, int n_terms, const ttn_c128* coeff, const int* term_ptr,
+                                   const int* factor_leaf, const ttn_c128* factor_mats,
+                                   const int64_t* factor_mat_off, int hermitian) {
+    if (c && c->plan.nset > 1)
+        return fail(c, TTN_E_INVALID, "the state is multi-set: use ttn_set_multiset_hamiltonian");
+    return set_ham(c, 1, n_terms, coeff, term_ptr, factor_leaf, factor_mats, factor_mat_off, nullptr, nullptr,
+                   hermitian);
+}
+
+ttn_status ttn_set_multiset_hamiltonian(ttn_ctx* c, int n_sets, int n_terms, const ttn_c128* coeff,
+                                        const int* term_ptr, const int* factor_leaf, const ttn_c128* factor_mats,
+                                        const int64_t* factor_mat_off, const int* bra, const int* ket,
+                                        int hermitian) {
+    if (!c) return TTN_E_INVALID;
+    if (n_sets < 1 || n_sets > TTN_MAX_SETS) return fail(c, TTN_E_INVALID, "n_sets must be in 1.." + std::to_string(TTN_MAX_SETS));
+    if (n_terms > 0 && (!bra || !ket)) return fail(c, TTN_E_INVALID, "null bra / ket set indices");
+    return set_ham(c, n_sets, n_terms, coeff, term_ptr, factor_leaf, factor_mats, factor_mat_off, bra, ket,
+                   hermitian);
+}
+
+ttn_status ttn_set_multiset_state(ttn_ctx* c, int n_sets, const ttn_c128* tensors, const int64_t* offsets) {
+    ttn_status u = usable(c); if (u) return u;
+    if (!tensors || !offsets) return fail(c, TTN_E_INVALID, "null tensors / offsets");
+    if (n_sets != c->plan.nset)
+        return fail(c, TTN_E_INVALID, "n_sets must equal the set count of the multi-set Hamiltonian (" +
+                    std::to_string(c->plan.nset) + ")");
+    const int n = c->tree.n;
+    std::vector<std::vector<cplx>> A(n);
+    for (int z = 0; z < n; ++z) A[z].resize((size_t)n_sets * c->tree.size[z]);
+    for (int a = 0; a < n_sets; ++a)
+        for (int z = 0; z < n; ++z) {
+            const int64_t i = (int64_t)a * n + z;
+            if (offsets[i + 1] - offsets[i] != c->tree.size[z])
+                return fail(c, TTN_E_INVALID, "tensor of set " + std::to_string(a) + ", node " + std::to_string(z) +
+                            " has the wrong size");
+            const cplx* p = (const cplx*)(tensors + offsets[i]);
+            for (int64_t q = 0; q < c->tree.size[z]; ++q) {
+                if (!std::isfinite(p[q].real()) || !std::isfinite(p[q].imag()))
+                    return fail(c, TTN_E_INVALID, "non-finite tensor entry");
+                A[z][a * c->tree.size[z] + q] = p[q];
+            }
+        }
+    return take_state(c, A);
+}
+
+ttn_status ttn_get_multiset_state(ttn_ctx* c, int alpha, ttn_c128* tensors, int64_t* offsets) {
+    if (!c || !tensors || !offsets) return TTN_E_INVALID;
+    if (alpha < 0 || alpha >= c->plan.nset) return fail(c, TTN_E_INVALID, "alpha outside the sets");
+    std::vector<std::vector<cplx>> A;
+    if (c->resident) {
+        cudaSetDevice(c->device);
+        ttn_status s = download_state(c, A);
+        if (s) return s;
+    }
+    const auto& src = c->resident ? A : c->host_A;
+    int64_t o = 0;
+    for (int z = 0; z < c->tree.n; ++z) {
+        offsets[z] = o;
+        std::memcpy(tensors + o, src[z].data() + (size_t)alpha * c->tree.size[z], c->tree.size[z] * 16);
+        o += c->tree.size[z];
+    }
+    offsets[c->tree.n] = o;
+    return TTN_OK;
+}
+
+ttn_status ttn_set_populations(ttn_ctx* c, double* pops) {
+    ttn_status u = ready(c); if (u) return u;
+    if (!pops) return fail(c, TTN_E_INVALID, "pops is NULL");
+    const int S = c->plan.nset;
+    if (S == 1) {
+        ttn_status s = ttn_norm_energy(c, &pops[0], nullptr);
+        return s;
+    }
+    ttn_status s = run_program(c, c->setpop_p, 0.0, 1);
+    if (s) return s;
+    std::vector<double> sc(2 * (size_t)S);
+    CK(cudaMemcpyAsync(sc.data(), c->d_state + c->plan.setpop_off, sc.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                       c->stream), "scalar copy");
+    CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+    for (int a = 0; a < S; ++a) pops[a] = sc[2 * a];
+    return TTN_OK;
+}
+
+ttn_status ttn_n_sets(const ttn_ctx* c, int* n_sets) {
+    if (!c || !n_sets) return TTN_E_INVALID;
+    *n_sets = c->plan.nset;
+    return TTN_OK;
 }
 
 ttn_status ttn_save(ttn_ctx* c, void* buf, size_t* len) {
     ttn_status u = usable(c); if (u) return u;
+    if (c->plan.nset > 1) return fail(c, TTN_E_INVALID, "checkpoints hold single-set states");
     if (!len) return fail(c, TTN_E_INVALID, "len is NULL");
     std::vector<std::vector<cplx>> A;
     int64_t steps = c->saved_steps;
@@ -748,6 +896,7 @@ ttn_status ttn_load(ttn_ctx* c, const void* buf, size_t len) {
     c->saved_flops = f0;
     c->saved_flops64 = f1;
     c->sop_coeff.clear(); c->sop_ptr.clear(); c->sop_leaf.clear(); c->sop_off.clear(); c->sop_mats.clear();
+    c->sop_nsets = 1; c->sop_bra.clear(); c->sop_ket.clear();
     if (has_h) {
         ttn_status s = ttn_set_sop_hamiltonian(c, (int)coeff.size(), (const ttn_c128*)coeff.data(), ptr.data(),
                                                leaf.empty() ? nullptr : leaf.data(),
@@ -767,13 +916,13 @@ ttn_status ttn_set_coefficients(ttn_ctx* c, int n_terms, const ttn_c128* coeff) 
     for (int r = 0; r < n_terms; ++r)
         if (!std::isfinite(coeff[r].re) || !std::isfinite(coeff[r].im)) return fail(c, TTN_E_INVALID, "non-finite coefficient");
     // replay the set-up with the stored factors (local copies: the call replaces them)
-    const std::vector<int> ptr = c->sop_ptr, leaf = c->sop_leaf;
+    const std::vector<int> ptr = c->sop_ptr, leaf = c->sop_leaf, bra = c->sop_bra, ket = c->sop_ket;
     const std::vector<cplx> mats = c->sop_mats;
     const std::vector<int64_t> off = c->sop_off;
-    return ttn_set_sop_hamiltonian(c, n_terms, coeff, ptr.empty() ? nullptr : ptr.data(),
-                                   leaf.empty() ? nullptr : leaf.data(),
-                                   mats.empty() ? nullptr : (const ttn_c128*)mats.data(),
-                                   off.empty() ? nullptr : off.data(), c->sop_herm);
+    return set_ham(c, c->sop_nsets, n_terms, coeff, ptr.empty() ? nullptr : ptr.data(),
+                   leaf.empty() ? nullptr : leaf.data(), mats.empty() ? nullptr : (const ttn_c128*)mats.data(),
+                   off.empty() ? nullptr : off.data(), bra.empty() ? nullptr : bra.data(),
+                   ket.empty() ? nullptr : ket.data(), c->sop_herm);
 }
 
 ttn_status ttn_step(ttn_ctx* c, double dt, int nsteps, const ttn_step_opts* opts) {
@@ -803,6 +952,7 @@ ttn_status ttn_ground_state(ttn_ctx* c, int nsweeps, double* energies) {
     ttn_status u = usable(c); if (u) return u;
     if (!c->has_h) return fail(c, TTN_E_STATE, "no Hamiltonian set");
     if (!c->ham.hermitian) return fail(c, TTN_E_INVALID, "ground-state sweeps need a Hermitian Hamiltonian");
+    if (c->plan.nset > 1) return fail(c, TTN_E_INVALID, "ground-state sweeps are for single-set states");
     if (nsweeps < 0) return fail(c, TTN_E_INVALID, "nsweeps must be >= 0");
     u = ready(c); if (u) return u;
     for (int i = 0; i < nsweeps; ++i) {
@@ -850,7 +1000,9 @@ ttn_status ttn_step_batch(ttn_ctx* const* ctxs, int n, double dt, int nsteps, co
         cluster = std::max(cluster, ctxs[i]->cluster_req > 0 ? std::max(ctxs[i]->cluster_req, need) : need);
     }
     CK(cudaMemcpyAsync(c->d_batch, ins.data(), sizeof(TtnInstance) * n, cudaMemcpyHostToDevice, c->stream), "batch upload");
-    int e = ttn_launch_program(c->precision, cluster, c->d_batch, n, dt, nsteps, c->stream);
+    bool tc = false;
+    for (int i = 0; i < n; ++i) tc |= ttn::ctx_uses_tc(ctxs[i]);
+    int e = ttn_launch_program(c->precision, cluster, c->d_batch, n, dt, nsteps, c->stream, tc);
     if (e != 0) return cuda_fail(c, (cudaError_t)e, "kernel launch");
     CK(cudaStreamSynchronize(c->stream), "stream synchronize");
     for (int i = 0; i < n; ++i) {
@@ -879,6 +1031,7 @@ ttn_status ttn_norm_energy(ttn_ctx* c, double* norm2, ttn_c128* energy) {
 
 ttn_status ttn_reduced_density(ttn_ctx* c, int leaf, ttn_c128* out) {
     ttn_status u = ready(c); if (u) return u;
+    if (c->plan.nset > 1) return fail(c, TTN_E_INVALID, "leaf densities are for single-set states: use ttn_set_populations");
     if (leaf < 0 || leaf >= c->tree.n || !c->tree.leaf(leaf) || !out) return fail(c, TTN_E_INVALID, "leaf must be a leaf node");
     ttn_status s = run_program(c, c->rdm_p[leaf], 0.0, 1);
     if (s) return s;
@@ -923,6 +1076,7 @@ ttn_status ttn_expect(ttn_ctx* c, int n_obs, const int* leaf, const ttn_c128* op
 
 ttn_status ttn_vacuum_projection(ttn_ctx* c, int keep_leaf, ttn_c128* out) {
     ttn_status u = ready(c); if (u) return u;
+    if (c->plan.nset > 1) return fail(c, TTN_E_INVALID, "vacuum projections are for single-set states");
     if (keep_leaf < 0 || keep_leaf >= c->tree.n || !c->tree.leaf(keep_leaf) || !out) return fail(c, TTN_E_INVALID, "keep_leaf must be a leaf");
     ttn_status s = run_program(c, c->vac_p[keep_leaf], 0.0, 1);
     if (s) return s;
@@ -937,6 +1091,7 @@ ttn_status ttn_vacuum_projection(ttn_ctx* c, int keep_leaf, ttn_c128* out) {
 
 ttn_status ttn_get_state(ttn_ctx* c, ttn_c128* tensors, int64_t* offsets) {
     if (!c || !tensors || !offsets) return TTN_E_INVALID;
+    if (c->plan.nset > 1) return fail(c, TTN_E_INVALID, "the state is multi-set: use ttn_get_multiset_state");
     std::vector<std::vector<cplx>> A;
     if (c->resident) {
         cudaSetDevice(c->device);
@@ -1115,7 +1270,8 @@ ttn_status ttn_autotune(ttn_ctx* c, double dt, int steps, int flags, double* tun
         if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_inst, &in, sizeof(in), cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
         if (e == cudaSuccess)
-            e = (cudaError_t)ttn_launch_program(c->precision, ttn::ctx_cluster(c), c->d_inst, 1, dt, steps, c->stream);
+            e = (cudaError_t)ttn_launch_program(c->precision, ttn::ctx_cluster(c), c->d_inst, 1, dt, steps,
+                                                c->stream, ttn::ctx_uses_tc(c));
         if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "autotune launch");
         ttn_status s2 = check_status(c);

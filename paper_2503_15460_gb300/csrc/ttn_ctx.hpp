@@ -46,7 +46,7 @@ struct ttn_ctx {
     size_t ops_bytes = 0;
     TtnSlot* d_slots = nullptr;
     TtnEntry* d_entries = nullptr;
-    ttn::DevProgram init_p, step_p, ne_p, spawn_p, ground_p;
+    ttn::DevProgram init_p, step_p, ne_p, spawn_p, ground_p, setpop_p;
     std::vector<ttn::DevProgram> rdm_p, vac_p, to_root_p;
     TtnInstance* d_inst = nullptr; // staging for single-instance launches
     TtnInstance* d_batch = nullptr;
@@ -60,6 +60,9 @@ struct ttn_ctx {
     std::vector<int> sop_ptr, sop_leaf;
     std::vector<int64_t> sop_off;
     int sop_herm = 1;
+    // multi-set operator as last given (ttn_set_multiset_hamiltonian)
+    int sop_nsets = 1;
+    std::vector<int> sop_bra, sop_ket;
     int64_t steps_total = 0;
     int64_t spawned = 0;            // single-particle functions added by expansion
     // Thread blocks per instance: 0 = chosen from the plan, 1 = one block,
@@ -84,6 +87,9 @@ constexpr int kSoloMaxDim = 45;
 // block per 4096 elements of the largest node tensor (a power of two, at
 // most 16); at least 2 when an index dimension exceeds kSoloMaxDim.
 int ctx_cluster(const ttn_ctx* c);
+// Some dimension of c's variant table asks for the tcgen05 mode product
+// (complex64 only): its launches take the build that carries it.
+bool ctx_uses_tc(const ttn_ctx* c);
 // Record a failure on c (or, for c == NULL, for ttn_last_error(NULL)).
 ttn_status ctx_fail(ttn_ctx* c, ttn_status s, const std::string& msg);
 // Bytes ctx_materialize allocates for the current plan.

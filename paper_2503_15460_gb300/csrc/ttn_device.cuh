@@ -30,6 +30,11 @@
 #include "ttn_program.h"
 #include "ttn_tc.cuh"
 
+// Builds with the tcgen05 mode product in the sweep kernel define this to 1.
+#ifndef TTN_WITH_TC
+#define TTN_WITH_TC 0
+#endif
+
 namespace {
 
 namespace cg = cooperative_groups;
@@ -331,7 +336,9 @@ __device__ double2 team_dot(const T* a, const T* b, int64_t n, Smem& sm, const T
 struct Shape {
     int D;
     int d[TTN_MAXD];
+    int nset = 1;           // set blocks (multi-set tensors: nset blocks of size() each, back to back)
     __device__ int64_t size() const { int64_t s = 1; for (int j = 0; j < D; ++j) s *= d[j]; return s; }
+    __device__ int64_t vlen() const { return size() * nset; }
     __device__ int64_t before(int k) const { int64_t s = 1; for (int j = 0; j < k; ++j) s *= d[j]; return s; }
     __device__ int64_t after(int k) const { int64_t s = 1; for (int j = k + 1; j < D; ++j) s *= d[j]; return s; }
 };
@@ -500,9 +507,12 @@ __device__ void mode_prod(T* out, const T* in, int64_t L, int nin, int nout, int
         mode_prod_simple(out, in, L, nin, nout, R, M, transM, w, accumulate, tm);
         return;
     }
+#if TTN_WITH_TC
     if constexpr (sizeof(T) == 8) {
         // tensor cores (3xTF32) where the variant table asks for them and the
-        // operands fit the staging area
+        // operands fit the staging area (only in the builds that carry the
+        // tensor-core path: a kernel holding tcgen05 code lost the overlap of
+        // two co-resident blocks per SM, so the default build has none)
         constexpr int stage = TM::wide ? kStageBytesClu : kStageBytes;
         if (s_mpv[nin] == 2 && s_tc_on && tc_fits(nin, stage)) {
             uint32_t ph = s_tc_phase;
@@ -518,6 +528,7 @@ __device__ void mode_prod(T* out, const T* in, int64_t L, int nin, int nout, int
             return;
         }
     }
+#endif
     if (nin > (sizeof(T) == 16 ? 16 : 32) || s_mpv[nin] != 0) {
         mode_prod_staged<T, (sizeof(T) == 16 ? 4 : 8)>(out, in, L, nin, R, M, w, accumulate, tm);
         return;
@@ -581,22 +592,33 @@ __device__ __forceinline__ int n_factors(const TtnEntry& e, int D) {
 // Entries are ordered so that those sharing their last factor (highest mode
 // with a matrix, same slot) are adjacent; their partial chains are summed in
 // t3 and the shared factor is applied once.
+// With sh.nset > 1 (multi-set, paper Sec. II.A) in and out hold nset blocks
+// of sh.size() elements; entry e reads block e.src and adds into block
+// e.dst, so out is cleared first and every entry accumulates.
 template <class T, class TM>
 __device__ void heff_apply(T* out, const T* in, T* t1, T* t2, T* t3, const Shape& sh, const TtnEntry* es, int ne,
                            const TtnSlot* slots, const TM& tm) {
     const int64_t S = sh.size();
+    const bool multi = sh.nset > 1;
     bool fresh = true;                          // out not written yet: the first term writes it
+    if (multi) {
+        for (int64_t q = tm.tid(); q < S * sh.nset; q += tm.nthr()) out[q] = czero<T>();
+        tm.sync();
+        fresh = false;
+    }
     int i = 0;
     while (i < ne) {
         const TtnEntry e = es[i];
         const double2 w = make_double2(e.wr, e.wi);
         const int lm = last_factor(e, sh.D);
+        const T* ine = multi ? in + (int64_t)e.src * S : in;
+        T* oute = multi ? out + (int64_t)e.dst * S : out;
         if (lm < 0) {
             const T wt = cT<T>(w);
             for (int64_t q = tm.tid(); q < S; q += tm.nthr()) {
-                T o = fresh ? czero<T>() : out[q];
-                cfma(o, wt, in[q]);
-                out[q] = o;
+                T o = fresh ? czero<T>() : oute[q];
+                cfma(o, wt, ine[q]);
+                oute[q] = o;
             }
             tm.sync();
             fresh = false;
@@ -606,19 +628,20 @@ __device__ void heff_apply(T* out, const T* in, T* t1, T* t2, T* t3, const Shape
         int j = i + 1;
         if (n_factors(e, sh.D) >= 2)
             while (j < ne && last_factor(es[j], sh.D) == lm && es[j].slot[lm] == e.slot[lm] &&
-                   n_factors(es[j], sh.D) >= 2) ++j;
+                   n_factors(es[j], sh.D) >= 2 && (!multi || es[j].dst == e.dst)) ++j;
         if (j - i == 1) {
-            apply_chain(in, t1, t2, sh, e, slots, -1, out, w, tm, !fresh);
+            apply_chain(ine, t1, t2, sh, e, slots, -1, oute, w, tm, !fresh);
             fresh = false;
             i = j;
             continue;
         }
         for (int q = i; q < j; ++q) {
             const TtnEntry eq = es[q];
-            apply_chain(in, t1, t2, sh, eq, slots, lm, t3, make_double2(eq.wr, eq.wi), tm, q > i);
+            const T* inq = multi ? in + (int64_t)eq.src * S : in;
+            apply_chain(inq, t1, t2, sh, eq, slots, lm, t3, make_double2(eq.wr, eq.wi), tm, q > i);
         }
         const int n = sh.d[lm];
-        mode_prod(out, (const T*)t3, sh.before(lm), n, n, sh.after(lm), (const T*)slots[e.slot[lm]].ptr, false,
+        mode_prod(oute, (const T*)t3, sh.before(lm), n, n, sh.after(lm), (const T*)slots[e.slot[lm]].ptr, false,
                   make_double2(1.0, 0.0), !fresh, tm);
         fresh = false;
         i = j;
@@ -760,12 +783,14 @@ __device__ void gram_acc(T* G, const T* X, const T* Y, const Shape& sh, int k, d
     }
 }
 
-// Environment build: for every output slot, out = Q^dag (sum_e w_e x_{j != keep} M_ej) Q.
-// The chains of all entries of one output are summed in ysum first, so each
-// output costs one Gram contraction.
+// Environment build: for every output slot, out = Q^dag (sum_e w_e x_{j != keep} M_ej) P
+// with P = Q (a single set) or the ket set's tensor (a cross-set
+// environment of a multi-set state, paper Sec. II.A).  The chains of all
+// entries of one output are summed in ysum first, so each output costs one
+// Gram contraction.
 template <class T, class TM>
-__device__ void env_build(const T* Q, T* t1, T* t2, T* ysum, const Shape& sh, int keep, const TtnEntry* es, int ne,
-                          const TtnSlot* slots, const TM& tm) {
+__device__ void env_build(const T* Q, const T* P, T* t1, T* t2, T* ysum, const Shape& sh, int keep,
+                          const TtnEntry* es, int ne, const TtnSlot* slots, const TM& tm) {
     const int64_t S = sh.size();
     int i = 0;
     while (i < ne) {
@@ -778,7 +803,7 @@ __device__ void env_build(const T* Q, T* t1, T* t2, T* ysum, const Shape& sh, in
         const T* Y;
         if (j - i == 1) {
             const TtnEntry e = es[i];
-            Y = apply_chain(Q, t1, t2, sh, e, slots, keep, (T*)nullptr, make_double2(1.0, 0.0), tm);
+            Y = apply_chain(P, t1, t2, sh, e, slots, keep, (T*)nullptr, make_double2(1.0, 0.0), tm);
             tm.sync();
             const long long tg = sub_start();
             gram_acc(out, Q, Y, sh, keep, make_double2(e.wr, e.wi), tm);
@@ -793,12 +818,12 @@ __device__ void env_build(const T* Q, T* t1, T* t2, T* ysum, const Shape& sh, in
                     const T wt = cT<T>(w);
                     for (int64_t x = tm.tid(); x < S; x += tm.nthr()) {
                         T o = q > i ? ysum[x] : czero<T>();
-                        cfma(o, wt, Q[x]);
+                        cfma(o, wt, P[x]);
                         ysum[x] = o;
                     }
                     tm.sync();
                 } else {
-                    apply_chain(Q, t1, t2, sh, e, slots, keep, ysum, w, tm, q > i);
+                    apply_chain(P, t1, t2, sh, e, slots, keep, ysum, w, tm, q > i);
                 }
             }
             const long long tg = sub_start();
@@ -1260,7 +1285,7 @@ __device__ int krylov_once(TS* x, const Shape& sh, const TtnEntry* es, int ne, c
                            int herm, double tol, int kmax, TB* V, int64_t smax, TB* t1, TB* t2, TB* t3, Smem& sm,
                            const TM& tm, int ground = 0) {
     double logbound = 0.0;          // log(|tau|^m prod h_{i+1,i} / m!)
-    const int64_t S = sh.size();
+    const int64_t S = sh.vlen();    // all set blocks form one vector
     const int64_t t0 = tm.tid(), ts = tm.nthr();
     double2 nb = make_double2(0.0, 0.0);
     for (int64_t i = t0; i < S; i += ts) nb.x += cabs2(cd(x[i]));
@@ -1520,8 +1545,13 @@ __device__ void small_gemm(double2* C, const double2* A, const double2* B, int m
 // E = X'^dag X' = V L V^dag and F = V L^{-1/2} (numerically nonzero part),
 // T = F^dag E C E F is Hermitian and its eigenvector w gives u = X' F w.
 template <class TS, class TB, class TM>
-__device__ __noinline__ void spawn_op(const TtnOp& op, const TtnInstance& in, Smem& sm, TB* V, int64_t smax, TB* t1, TB* t2,
-                         double2* Wc, double2* Qc, const TM& tm) {
+__device__ __noinline__ void spawn_op(const TtnOp* opg, const TtnInstance* ing, Smem& sm, TB* V, int64_t smax, TB* t1,
+                                      TB* t2, double2* Wc, double2* Qc, const TM& tm) {
+    // The op and the instance are read from global memory: a reference to
+    // the caller's register copies would force those copies into local
+    // memory for the whole kernel.
+    const TtnOp& op = *opg;
+    const TtnInstance& in = *ing;
     const int t0 = tm.tid(), ts = tm.nthr();
     Shape shz, shc;
     shz.D = op.D; shc.D = op.Dc;
@@ -1791,12 +1821,14 @@ __device__ __noinline__ void spawn_op(const TtnOp& op, const TtnInstance& in, Sm
 // interpreter: TS = node tensor / bond type, TB = bulk type
 // ---------------------------------------------------------------------------
 template <class TS, class TB, class TM>
-__device__ void run_op(const TtnOp& op, const TtnInstance& in, double dt, Smem& sm, const TM& tm) {
+__device__ void run_op(const TtnOp& op, const TtnInstance& in, const TtnOp* opg, const TtnInstance* ing, double dt,
+                       Smem& sm, const TM& tm) {
     const int t0 = tm.tid(), ts = tm.nthr();
     const bool lead = threadIdx.x == 0 && tm.rank() == 0;
     Shape sh;
     sh.D = op.D;
     for (int j = 0; j < TTN_MAXD; ++j) sh.d[j] = j < op.D ? op.dims[j] : 1;
+    sh.nset = op.nset > 1 ? op.nset : 1;
     TB* work = (TB*)in.work;
     TB* V = work;                                       // TTN_KMAX + 1 Krylov vectors
     TB* t1 = work + (int64_t)(TTN_KMAX + 1) * in.smax;
@@ -1852,9 +1884,10 @@ __device__ void run_op(const TtnOp& op, const TtnInstance& in, double dt, Smem& 
         tm.sync();
         break;
     }
-    case TTN_OP_ENV: {                // Krylov vectors are free here: V[0] holds Q, V[1] the chain sum
+    case TTN_OP_ENV: {                // Krylov vectors are free here: V[0] holds Q, V[1] the chain sum, V[2] P
         const TB* Q = as_bulk<TB>((const TS*)op.a, V, sh.size(), tm);
-        env_build(Q, t1, t2, V + in.smax, sh, op.k, es, op.ne, in.slots, tm);
+        const TB* P = op.c ? as_bulk<TB>((const TS*)op.c, V + 2 * in.smax, sh.size(), tm) : Q;
+        env_build(Q, P, t1, t2, V + in.smax, sh, op.k, es, op.ne, in.slots, tm);
         break;
     }
     case TTN_OP_COMBO:
@@ -1881,12 +1914,12 @@ __device__ void run_op(const TtnOp& op, const TtnInstance& in, double dt, Smem& 
     case TTN_OP_DOT: {
         double2 r;
         if (op.ne > 0) {
-            const TB* A = as_bulk<TB>((const TS*)op.a, V, sh.size(), tm);
+            const TB* A = as_bulk<TB>((const TS*)op.a, V, sh.vlen(), tm);
             heff_apply(t1, A, t2, V + in.smax, t3, sh, es, op.ne, in.slots, tm);
-            r = team_dot(A, (const TB*)t1, sh.size(), sm, tm);
+            r = team_dot(A, (const TB*)t1, sh.vlen(), sm, tm);
         } else {
             const TS* A = (const TS*)op.a;
-            r = team_dot(A, A, sh.size(), sm, tm);
+            r = team_dot(A, A, sh.vlen(), sm, tm);
         }
         if (lead) { op.out[0] = r.x; op.out[1] = r.y; }
         tm.sync();
@@ -1910,13 +1943,13 @@ __device__ void run_op(const TtnOp& op, const TtnInstance& in, double dt, Smem& 
         break;
     }
     case TTN_OP_SPAWN:
-        spawn_op<TS, TB>(op, in, sm, V, in.smax, t1, t2, Wc, Qc, tm);
+        spawn_op<TS, TB>(opg, ing, sm, V, in.smax, t1, t2, Wc, Qc, tm);
         break;
     case TTN_OP_PHASE: {             // a <- exp(-i tau_coef dt) a
         TS* A = (TS*)op.a;
         const double th = op.tau_coef * dt;
         const double2 f = make_double2(cos(th), -sin(th));
-        for (int64_t i = t0; i < sh.size(); i += ts) A[i] = cT<TS>(cmul(f, cd(A[i])));
+        for (int64_t i = t0; i < sh.vlen(); i += ts) A[i] = cT<TS>(cmul(f, cd(A[i])));
         tm.sync();
         break;
     }
@@ -1983,8 +2016,14 @@ __global__ void __launch_bounds__(TM::NT, TM::wide ? 1 : 2) program_kernel(const
         for (int i = 0; i < 8; ++i) s_sub[i] = 0;
         s_t0 = global_ns();
     }
-    for (int i = threadIdx.x; i <= TTN_MAXCHI; i += TM::NT) s_mpv[i] = in.mp_variant[i];
+    // (from global memory: indexing the local copy's array would place the
+    // whole copy in local memory)
+    for (int i = threadIdx.x; i <= TTN_MAXCHI; i += TM::NT) s_mpv[i] = insts[b].mp_variant[i];
+#if TTN_WITH_TC
     const bool use_tc = sizeof(TB) == 8 && in.use_tc != 0;
+#else
+    constexpr bool use_tc = false;           // this build has no tensor-core path
+#endif
     if (threadIdx.x == 0) { s_tc_on = use_tc ? 1 : 0; s_tc_phase = 0; s_tc_status = in.status; }
     if (use_tc) {
         if ((threadIdx.x >> 5) == 0) tc_alloc(&s_tc_taddr, kTcCols);
@@ -2004,7 +2043,7 @@ __global__ void __launch_bounds__(TM::NT, TM::wide ? 1 : 2) program_kernel(const
             if (st != 0) { stopped = true; break; }
             const TtnOp op = in.ops[o];
             const long long c0 = clock64();
-            run_op<TS, TB>(op, in, dtb, sm, tm);
+            run_op<TS, TB>(op, in, in.ops + o, insts + b, dtb, sm, tm);
             if (threadIdx.x == 0 && s_count && in.op_cycles)
                 atomicAdd(&in.op_cycles[op.type & 15], (unsigned long long)(clock64() - c0));
         }

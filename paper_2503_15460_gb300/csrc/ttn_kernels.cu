@@ -58,6 +58,8 @@ int ttn_program_init() {
     if (!e) e = ttn_variant_mix_solo_init();
     if (!e) e = ttn_variant_f64_clu_init();
     if (!e) e = ttn_variant_mix_clu_init();
+    if (!e) e = ttn_variant_mix_solo_tc_init();
+    if (!e) e = ttn_variant_mix_clu_tc_init();
     return e;
 }
 
@@ -67,16 +69,18 @@ int ttn_cluster_capacity(int precision, int cluster, int* max_active) {
 }
 
 int ttn_launch_program(int precision, int cluster, const TtnInstance* d_insts, int n_inst, double dt, int nrep,
-                       cudaStream_t s) {
-    return ttn_launch_program_ex(precision, cluster, d_insts, nullptr, n_inst, dt, nrep, 0, nullptr, s);
+                       cudaStream_t s, int tc) {
+    return ttn_launch_program_ex(precision, cluster, d_insts, nullptr, n_inst, dt, nrep, 0, nullptr, s, tc);
 }
 
 int ttn_launch_program_ex(int precision, int cluster, const TtnInstance* d_insts, const TtnLaunchHdr* d_hdr,
-                          int n_inst, double dt, int nrep, long long slice_ns, TtnRepOut* d_rep_out, cudaStream_t s) {
+                          int n_inst, double dt, int nrep, long long slice_ns, TtnRepOut* d_rep_out, cudaStream_t s,
+                          int tc) {
     if (n_inst <= 0) return 0;
     TtnVariantArgs a{d_insts, d_hdr, n_inst, cluster, dt, nrep, slice_ns, d_rep_out, s};
-    if (cluster <= 1) return precision == 0 ? ttn_variant_f64_solo(a) : ttn_variant_mix_solo(a);
-    return precision == 0 ? ttn_variant_f64_clu(a) : ttn_variant_mix_clu(a);
+    if (precision == 0) return cluster <= 1 ? ttn_variant_f64_solo(a) : ttn_variant_f64_clu(a);
+    if (tc) return cluster <= 1 ? ttn_variant_mix_solo_tc(a) : ttn_variant_mix_clu_tc(a);
+    return cluster <= 1 ? ttn_variant_mix_solo(a) : ttn_variant_mix_clu(a);
 }
 
 // ---------------------------------------------------------------------------

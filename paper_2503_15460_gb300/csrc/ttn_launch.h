@@ -11,9 +11,12 @@
 // Run the op list of each instance nrep times.  cluster <= 1: one thread
 // block (256 threads) per instance; cluster = 2..16: one thread-block
 // cluster of that many blocks (512 threads each) per instance.
-// precision: 0 = complex128, 1 = complex64 bulk.  Returns a cudaError_t code.
+// precision: 0 = complex128, 1 = complex64 bulk.  tc = 1 (complex64 only)
+// launches the build that carries the tcgen05 mode product (instances whose
+// variant table asks for tensor cores); with tc = 0 such dimensions take
+// the staged FFMA routine.  Returns a cudaError_t code.
 int ttn_launch_program(int precision, int cluster, const TtnInstance* d_insts, int n_inst, double dt, int nrep,
-                       cudaStream_t stream);
+                       cudaStream_t stream, int tc = 0);
 
 // General form: `n_inst` instances (grid n_inst x cluster blocks).  With
 // d_hdr (device memory) the first d_hdr->n instances run and
@@ -24,7 +27,7 @@ int ttn_launch_program(int precision, int cluster, const TtnInstance* d_insts, i
 // what each instance did.
 int ttn_launch_program_ex(int precision, int cluster, const TtnInstance* d_insts, const TtnLaunchHdr* d_hdr,
                           int n_inst, double dt, int nrep, long long slice_ns, TtnRepOut* d_rep_out,
-                          cudaStream_t stream);
+                          cudaStream_t stream, int tc = 0);
 
 // Set the kernel attributes of every variant on the current device (call
 // before capturing a launch into a CUDA graph).  Returns a cudaError_t code.
@@ -90,3 +93,8 @@ int ttn_variant_f64_clu_init();
 int ttn_variant_mix_clu_init();
 int ttn_variant_f64_clu_capacity(int cluster, int* max_active);
 int ttn_variant_mix_clu_capacity(int cluster, int* max_active);
+// the complex64 builds with the tcgen05 mode product
+int ttn_variant_mix_solo_tc(const TtnVariantArgs& a);
+int ttn_variant_mix_clu_tc(const TtnVariantArgs& a);
+int ttn_variant_mix_solo_tc_init();
+int ttn_variant_mix_clu_tc_init();

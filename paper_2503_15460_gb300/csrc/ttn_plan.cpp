@@ -23,6 +23,7 @@
 #include <functional>
 #include <set>
 #include <sstream>
+#include <tuple>
 
 namespace ttn {
 
@@ -198,13 +199,16 @@ std::string build_tree(int n, const int* parent, const int* phys, const int* bon
 
 std::string build_hamiltonian(const Tree& t, int n_terms, const cplx* coeff, const int* term_ptr,
                               const int* factor_leaf, const cplx* mats, const int64_t* mat_off,
-                              int hermitian, Hamiltonian& h) {
+                              int hermitian, Hamiltonian& h, int n_sets, const int* bra, const int* ket) {
     std::ostringstream err;
     if (n_terms < 1) return "n_terms must be >= 1";
     if (!coeff || !term_ptr) return "null coefficient / term_ptr";
     if (term_ptr[0] != 0) return "term_ptr[0] must be 0";
+    if (n_sets < 1 || n_sets > TTN_MAX_SETS) return "n_sets must be in 1.." + std::to_string(TTN_MAX_SETS);
+    if (n_sets > 1 && (!bra || !ket)) return "a multi-set operator needs bra and ket set indices";
     h = Hamiltonian();
     h.hermitian = hermitian != 0;
+    h.n_sets = n_sets;
     std::map<std::pair<int, std::vector<double>>, int> dedup;
     for (int r = 0; r < n_terms; ++r) {
         if (term_ptr[r + 1] < term_ptr[r]) return "term_ptr must be non-decreasing";
@@ -233,11 +237,18 @@ std::string build_hamiltonian(const Tree& t, int n_terms, const cplx* coeff, con
         std::sort(key.begin(), key.end());
         for (size_t i = 1; i < key.size(); ++i)
             if (key[i].first == key[i - 1].first) { err << "term " << r << " has two factors on leaf " << key[i].first; return err.str(); }
+        if (n_sets > 1 && (bra[r] < 0 || bra[r] >= n_sets || ket[r] < 0 || ket[r] >= n_sets)) {
+            err << "term " << r << " names a set outside 0.." << n_sets - 1; return err.str();
+        }
         if (coeff[r] == cplx(0.0)) continue;
         h.coeff.push_back(coeff[r]);
         h.terms.push_back(key);
+        if (n_sets > 1) { h.bra.push_back(bra[r]); h.ket.push_back(ket[r]); }
     }
-    if (h.coeff.empty()) { h.coeff.push_back(0.0); h.terms.push_back({}); }
+    if (h.coeff.empty()) {
+        h.coeff.push_back(0.0); h.terms.push_back({});
+        if (n_sets > 1) { h.bra.push_back(0); h.ket.push_back(0); }
+    }
     return "";
 }
 
@@ -250,6 +261,7 @@ struct Proto {
     cplx w;
     int out;
     std::vector<int> slot;
+    int src = 0, dst = 0;   // multi-set: ket and bra set of the entry
 };
 
 struct Builder {
@@ -1079,11 +1091,303 @@ struct Builder {
     }
 };
 
+// ---------------------------------------------------------------------------
+// Multi-set operators (paper Sec. II.A, multi-set ansatz).  Every set has its
+// own tensors on the shared tree; term r = c_r |a_r><b_r| (x) (factors).
+// A channel is keyed by (bra set, ket set, part of the term on one side of
+// a bond) and stands for that part's matrix element between the bra set's
+// and the ket set's functions there.  Only a same-set channel with an empty
+// part is the identity; for a != b an empty part is the overlap of the two
+// sets' functions, a real matrix.  No further grouping: terms with the same
+// set pair and the same part share the channel.
+// ---------------------------------------------------------------------------
+struct MsBuilder {
+    const Tree& t;
+    const Hamiltonian& h;
+    Plan& p;
+    const int S;
+    using CKey = std::tuple<int, int, Key>;
+    struct Def { int up; int c; CKey key; int slot; };
+    std::vector<std::map<CKey, int>> up_ch, dn_ch;       // per bond (child node)
+    std::vector<Def> todo;
+    std::map<std::pair<int, int>, int> phys;             // (leaf, matrix id) -> constant slot
+    // ENV entries per bond and set pair: built at the child (up) or at the
+    // parent keeping the child's mode (down)
+    std::vector<std::map<std::pair<int, int>, std::vector<Proto>>> up_env, dn_env;
+    std::vector<std::pair<int, int>> heff_rng, bond_rng;
+    std::vector<std::map<std::pair<int, int>, std::pair<int, int>>> up_rng, dn_rng;
+
+    MsBuilder(const Tree& t_, const Hamiltonian& h_, Plan& p_) : t(t_), h(h_), p(p_), S(h_.n_sets) {
+        up_ch.resize(t.n); dn_ch.resize(t.n); up_env.resize(t.n); dn_env.resize(t.n);
+    }
+    int new_slot(int rows, int cols) {
+        SlotInfo s; s.rows = rows; s.cols = cols;
+        p.slots.push_back(s);
+        return (int)p.slots.size() - 1;
+    }
+    Key restrict_to(const Key& k, int c, bool inside) const {
+        Key out;
+        for (auto& f : k) if (t.in_sub(f.first, c) == inside) out.push_back(f);
+        return out;
+    }
+    int phys_slot(int l, int m) {
+        auto it = phys.find({l, m});
+        if (it != phys.end()) return it->second;
+        int d = t.phys[l];
+        int id = new_slot(d, d);
+        p.slots[id].constant = true;
+        p.slots[id].data = h.mats[m];
+        return phys[{l, m}] = id;
+    }
+    // channel of bond c (created on first use; -1 = identity)
+    int chan(bool up, int c, int a, int b, const Key& part) {
+        if (a == b && part.empty()) return -1;
+        auto& m = up ? up_ch[c] : dn_ch[c];
+        CKey key{a, b, part};
+        auto it = m.find(key);
+        if (it != m.end()) return it->second;
+        int s = new_slot(t.bond[c], t.bond[c]);
+        m[key] = s;
+        todo.push_back({up ? 1 : 0, c, key, s});
+        return s;
+    }
+    // slot list of a term part `key` (the whole term, or its part on one
+    // side of a bond) on the modes of node z, skipping mode `skip`
+    std::vector<int> mode_slots(int z, int a, int b, const Key& key, int skip) {
+        const int D = (int)t.dims[z].size();
+        std::vector<int> sl(D, -1);
+        if (t.leaf(z)) {
+            if (skip != 0) {
+                Key in = restrict_to(key, z, true);
+                if (!in.empty()) sl[0] = phys_slot(z, in[0].second);
+            }
+        } else {
+            for (size_t k = 0; k < t.ch[z].size(); ++k) {
+                if ((int)k == skip) continue;
+                int ck = t.ch[z][k];
+                sl[k] = chan(true, ck, a, b, restrict_to(key, ck, true));
+            }
+        }
+        if (z > 0 && skip != D - 1) sl[D - 1] = chan(false, z, a, b, restrict_to(key, z, false));
+        return sl;
+    }
+    void define(const Def& q) {
+        const int a = std::get<0>(q.key), b = std::get<1>(q.key);
+        const Key& part = std::get<2>(q.key);
+        Proto e;
+        e.w = 1.0;
+        e.out = q.slot;
+        if (q.up) {
+            // at node c, every mode but the parent's
+            e.slot = mode_slots(q.c, a, b, part, (int)t.dims[q.c].size() - 1);
+            up_env[q.c][{a, b}].push_back(e);
+        } else {
+            // at the parent z keeping the mode of c; part is the part outside c
+            const int z = t.parent[q.c];
+            const int k = (int)(std::find(t.ch[z].begin(), t.ch[z].end(), q.c) - t.ch[z].begin());
+            e.slot = mode_slots(z, a, b, part, k);
+            dn_env[q.c][{a, b}].push_back(e);
+        }
+    }
+    void close() {
+        for (size_t i = 0; i < todo.size(); ++i) {
+            const Def q = todo[i];          // define() may grow todo
+            define(q);
+        }
+    }
+
+    // ---- entries -------------------------------------------------------------
+    // Entries with the same (dst, src, slots) are merged; the order keeps
+    // entries of one output slot, then of one destination set, then of one
+    // last factor adjacent (the device sums such runs before their shared
+    // last factor).
+    std::pair<int, int> push(std::vector<Proto> es) {
+        std::map<std::tuple<int, int, int, std::vector<int>>, cplx> merged;
+        std::vector<std::tuple<int, int, int, std::vector<int>>> order;
+        for (auto& e : es) {
+            auto key = std::make_tuple(e.out, e.dst, e.src, e.slot);
+            if (!merged.count(key)) order.push_back(key);
+            merged[key] += e.w;
+        }
+        std::vector<Proto> out;
+        for (auto& key : order) {
+            if (merged[key] == cplx(0.0) && std::get<0>(key) < 0) continue;
+            Proto e;
+            e.w = merged[key]; e.out = std::get<0>(key); e.dst = std::get<1>(key); e.src = std::get<2>(key);
+            e.slot = std::get<3>(key);
+            out.push_back(e);
+        }
+        auto last = [](const Proto& e) {
+            int lm = -1;
+            for (size_t j = 0; j < e.slot.size(); ++j) if (e.slot[j] >= 0) lm = (int)j;
+            return std::make_pair(lm, lm >= 0 ? e.slot[lm] : -1);
+        };
+        std::stable_sort(out.begin(), out.end(), [&](const Proto& a, const Proto& b) {
+            if (a.out != b.out) return a.out < b.out;
+            if (a.dst != b.dst) return a.dst < b.dst;
+            return last(a) < last(b);
+        });
+        int e0 = (int)p.entries.size();
+        for (auto& e : out) {
+            TtnEntry te{};
+            te.wr = e.w.real(); te.wi = e.w.imag(); te.out = e.out; te.src = e.src; te.dst = e.dst;
+            for (int j = 0; j < TTN_MAXD; ++j) te.slot[j] = j < (int)e.slot.size() ? e.slot[j] : -1;
+            p.entries.push_back(te);
+        }
+        return {e0, (int)out.size()};
+    }
+
+    void prepare() {
+        const int n = t.n, R = (int)h.terms.size();
+        std::vector<std::vector<Proto>> heff(n), bond(n);
+        p.op_bond_dim.assign(n, 0);
+        for (int z = 0; z < n; ++z) {
+            for (int r = 0; r < R; ++r) {
+                Proto e;
+                e.w = h.coeff[r]; e.out = -1; e.dst = h.bra[r]; e.src = h.ket[r];
+                e.slot = mode_slots(z, h.bra[r], h.ket[r], h.terms[r], -1);
+                heff[z].push_back(e);
+                if (z == 0) continue;
+                Proto f;
+                f.w = h.coeff[r]; f.out = -1; f.dst = h.bra[r]; f.src = h.ket[r];
+                f.slot = {chan(true, z, h.bra[r], h.ket[r], restrict_to(h.terms[r], z, true)),
+                          chan(false, z, h.bra[r], h.ket[r], restrict_to(h.terms[r], z, false))};
+                bond[z].push_back(f);
+            }
+        }
+        close();
+        heff_rng.assign(n, {0, 0}); bond_rng.assign(n, {0, 0});
+        up_rng.assign(n, {}); dn_rng.assign(n, {});
+        for (int z = 0; z < n; ++z) {
+            heff_rng[z] = push(heff[z]);
+            if (z == 0) continue;
+            bond_rng[z] = push(bond[z]);
+            p.op_bond_dim[z] = (int)(up_ch[z].size() + dn_ch[z].size());
+            for (auto& kv : up_env[z]) up_rng[z][kv.first] = push(kv.second);
+            for (auto& kv : dn_env[z]) dn_rng[z][kv.first] = push(kv.second);
+        }
+    }
+
+    // ---- programs --------------------------------------------------------------
+    int64_t set_off(int z, int a) const { return p.tensor_off[z] + (int64_t)a * t.size[z] * (int64_t)p.esz_state; }
+    int64_t bond_buf(int a, int nb) const { return p.bond_off + (int64_t)a * nb * nb * (int64_t)p.esz_state; }
+    OpSpec base(int type, int z, int k) const {
+        OpSpec s;
+        std::memset(&s.op, 0, sizeof(TtnOp));
+        s.op.type = type;
+        s.op.D = (int)t.dims[z].size();
+        for (int j = 0; j < s.op.D; ++j) s.op.dims[j] = t.dims[z][j];
+        s.op.k = k;
+        return s;
+    }
+    void per_set(Program& pr, int type, int z, int k, int bond_child) {
+        for (int a = 0; a < S; ++a) {
+            OpSpec s = base(type, z, k);
+            s.a_off = set_off(z, a);
+            s.b_off = bond_buf(a, t.bond[bond_child]);
+            pr.ops.push_back(s);
+        }
+    }
+    void emit_env(Program& pr, int z, int k, const std::map<std::pair<int, int>, std::pair<int, int>>& rngs) {
+        for (auto& kv : rngs) {
+            if (kv.second.second == 0) continue;
+            OpSpec s = base(TTN_OP_ENV, z, k);
+            s.a_off = set_off(z, kv.first.first);
+            if (kv.first.second != kv.first.first) s.c_off = set_off(z, kv.first.second);
+            s.op.e0 = kv.second.first; s.op.ne = kv.second.second;
+            pr.ops.push_back(s);
+        }
+    }
+    void emit_env_up(Program& pr, int c) { emit_env(pr, c, (int)t.dims[c].size() - 1, up_rng[c]); }
+    void emit_env_down(Program& pr, int z, int k) { emit_env(pr, z, k, dn_rng[t.ch[z][k]]); }
+    void emit_evolve_node(Program& pr, int z) {
+        OpSpec s = base(TTN_OP_EVOLVE, z, 0);
+        s.a_off = p.tensor_off[z];
+        s.op.nset = S;
+        s.op.e0 = heff_rng[z].first; s.op.ne = heff_rng[z].second;
+        s.op.hermitian = h.hermitian ? 1 : 0;
+        s.op.tau_coef = 0.5;
+        pr.ops.push_back(s);
+    }
+    void emit_evolve_bond(Program& pr, int c) {
+        OpSpec s;
+        std::memset(&s.op, 0, sizeof(TtnOp));
+        s.op.type = TTN_OP_EVOLVE;
+        s.op.D = 2;
+        s.op.dims[0] = s.op.dims[1] = t.bond[c];
+        s.a_off = p.bond_off;
+        s.op.nset = S;
+        s.op.e0 = bond_rng[c].first; s.op.ne = bond_rng[c].second;
+        s.op.hermitian = h.hermitian ? 1 : 0;
+        s.op.tau_coef = -0.5;                    // backward bond step
+        pr.ops.push_back(s);
+    }
+    // The projector-splitting sweeps of the single-set plan, with the gauge
+    // moves done set by set and the exponentials on all sets at once.
+    void emit_S(Program& pr, int z) {
+        for (size_t k = 0; k < t.ch[z].size(); ++k) {
+            const int c = t.ch[z][k], Dc = (int)t.dims[c].size();
+            per_set(pr, TTN_OP_QR_DOWN, z, (int)k, c);
+            per_set(pr, TTN_OP_ABSORB_CHILD, c, Dc - 1, c);
+            emit_env_down(pr, z, (int)k);
+            emit_S(pr, c);
+            per_set(pr, TTN_OP_QR_UP, c, Dc - 1, c);
+            emit_env_up(pr, c);
+            emit_evolve_bond(pr, c);
+            per_set(pr, TTN_OP_ABSORB_PARENT, z, (int)k, c);
+        }
+        emit_evolve_node(pr, z);
+    }
+    void emit_Sstar(Program& pr, int z) {
+        emit_evolve_node(pr, z);
+        for (int k = (int)t.ch[z].size() - 1; k >= 0; --k) {
+            const int c = t.ch[z][k], Dc = (int)t.dims[c].size();
+            per_set(pr, TTN_OP_QR_DOWN, z, k, c);
+            emit_env_down(pr, z, k);
+            emit_evolve_bond(pr, c);
+            per_set(pr, TTN_OP_ABSORB_CHILD, c, Dc - 1, c);
+            emit_Sstar(pr, c);
+            per_set(pr, TTN_OP_QR_UP, c, Dc - 1, c);
+            emit_env_up(pr, c);
+            per_set(pr, TTN_OP_ABSORB_PARENT, z, k, c);
+        }
+    }
+    void make_programs() {
+        for (int z : t.postorder())
+            if (z > 0) emit_env_up(p.init_prog, z);
+        emit_S(p.step_prog, 0);
+        emit_Sstar(p.step_prog, 0);
+        OpSpec end;
+        std::memset(&end.op, 0, sizeof(TtnOp));
+        end.op.type = TTN_OP_STEP_END;
+        p.step_prog.ops.push_back(end);
+        // norm and energy of the whole state, populations of the sets
+        OpSpec nrm = base(TTN_OP_DOT, 0, 0);
+        nrm.a_off = p.tensor_off[0]; nrm.op.nset = S; nrm.out_off = p.scal_off;
+        p.norm_energy_prog.ops.push_back(nrm);
+        OpSpec en = base(TTN_OP_DOT, 0, 0);
+        en.a_off = p.tensor_off[0]; en.op.nset = S;
+        en.op.e0 = heff_rng[0].first; en.op.ne = heff_rng[0].second;
+        en.out_off = p.scal_off + 16;
+        p.norm_energy_prog.ops.push_back(en);
+        for (int a = 0; a < S; ++a) {
+            OpSpec d = base(TTN_OP_DOT, 0, 0);
+            d.a_off = set_off(0, a); d.out_off = p.setpop_off + 16 * a;
+            p.setpop_prog.ops.push_back(d);
+        }
+        p.to_root_prog.assign(t.n, {});
+        p.rdm_prog.assign(t.n, {}); p.rdm_slot.assign(t.n, -1);
+        p.vac_prog.assign(t.n, {}); p.vac_slot.assign(t.n, -1);
+    }
+};
+
 }  // namespace
 
 std::string make_plan(const Tree& t, const Hamiltonian* h, int precision, Plan& p) {
     p = Plan();
     p.esz = precision == 1 ? 8 : 16;   // 1: mixed precision (complex64 bulk)
+    const int nset = (h && h->n_sets > 1) ? h->n_sets : 1;
+    p.nset = nset;
     // ---- state arena --------------------------------------------------------
     int64_t off = 0;
     p.tensor_off.assign(t.n, 0);
@@ -1091,15 +1395,15 @@ std::string make_plan(const Tree& t, const Hamiltonian* h, int precision, Plan& 
     int max_chi = 1;
     for (int z = 0; z < t.n; ++z) {
         p.tensor_off[z] = off;
-        off = align_up(off + t.size[z] * (int64_t)p.esz_state, 256);
+        off = align_up(off + nset * t.size[z] * (int64_t)p.esz_state, 256);
         smax = std::max(smax, t.size[z]);
         for (int d : t.dims[z]) max_chi = std::max(max_chi, d);
     }
-    smax = std::max<int64_t>(smax, (int64_t)max_chi * max_chi);
+    smax = std::max<int64_t>(smax, (int64_t)max_chi * max_chi) * nset;   // Krylov vectors span all sets
     p.max_chi = max_chi;
     p.smax = align_up(smax, 32);
     p.bond_off = off;
-    off = align_up(off + (int64_t)max_chi * max_chi * 16, 256);
+    off = align_up(off + (int64_t)nset * max_chi * max_chi * 16, 256);
     p.work_off = off;
     // (KMAX+1) Krylov vectors + 3 scratch tensors in the bulk type, then 2
     // FP64 QR matrices
@@ -1118,7 +1422,23 @@ std::string make_plan(const Tree& t, const Hamiltonian* h, int precision, Plan& 
     }
     p.max_stamps = 4096;
     p.stamps_off = off; off = align_up(off + 8 * (int64_t)p.max_stamps, 256);
+    p.setpop_off = off; off = align_up(off + 16 * (int64_t)nset, 256);
     p.total_bytes = off;
+
+    if (nset > 1) {
+        // multi-set state: per-pair channels, no expansion / ground state / RDM programs
+        MsBuilder mb(t, *h, p);
+        mb.prepare();
+        mb.make_programs();
+        p.spawn_kmax = 0;
+        p.spawn_ws_off = p.total_bytes;
+        int64_t soff = 0;
+        for (auto& sl : p.slots) {
+            sl.off = soff;
+            soff = align_up(soff + (int64_t)sl.rows * sl.cols * (int64_t)p.esz, 256);
+        }
+        return "";
+    }
 
     // ---- operators and programs ---------------------------------------------
     Builder b(t, h, p);

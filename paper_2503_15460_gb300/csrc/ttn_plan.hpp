@@ -37,11 +37,17 @@ struct Hamiltonian {
     std::vector<std::vector<cplx>> mats;    // distinct factor matrices (row-major d x d)
     std::vector<int> mat_dim;
     bool hermitian = true;
+    // Multi-set operator (paper Sec. II.A, multi-set ansatz): term r is
+    // c_r |bra[r]><ket[r]| (x) (its factors); n_sets = 1 (bra, ket empty)
+    // for the single-set SOP.
+    int n_sets = 1;
+    std::vector<int> bra, ket;
 };
 
 std::string build_hamiltonian(const Tree& t, int n_terms, const cplx* coeff, const int* term_ptr,
                               const int* factor_leaf, const cplx* mats, const int64_t* mat_off,
-                              int hermitian, Hamiltonian& h);
+                              int hermitian, Hamiltonian& h, int n_sets = 1, const int* bra = nullptr,
+                              const int* ket = nullptr);
 
 // Device-side storage kinds.  Offsets are in bytes from the arena base.
 struct SlotInfo {
@@ -54,7 +60,7 @@ struct SlotInfo {
 // An operation before linking: a/b/out hold arena byte offsets, or -1.
 struct OpSpec {
     TtnOp op;
-    int64_t a_off = -1, b_off = -1, out_off = -1;
+    int64_t a_off = -1, b_off = -1, out_off = -1, c_off = -1;   // c_off: ENV ket tensor
 };
 
 struct Program {
@@ -65,6 +71,11 @@ struct Plan {
     // arena layout (bytes)
     size_t esz = 16;                 // bytes per complex element of the bulk type (slots, Krylov)
     size_t esz_state = 16;           // bytes per element of node tensors / bond buffer (complex128)
+    // Set blocks per node tensor (multi-set state, paper Sec. II.A): node z
+    // holds nset tensors of t.size[z] elements back to back at tensor_off[z]
+    // (set 0 first); the bond buffer holds nset bond matrices of the bond
+    // being moved, each bond x bond, back to back.
+    int nset = 1;
     std::vector<int64_t> tensor_off;
     int64_t bond_off = 0, work_off = 0, status_off = 0, steps_off = 0, stamps_off = 0, scal_off = 0, flops_off = 0, cycles_off = 0;
     int64_t smax = 0;                // elements per workspace vector
@@ -96,6 +107,8 @@ struct Plan {
     int spawn_kmax = 0;
     // observables
     Program norm_energy_prog;        // out scalars 0: <A,A>, 1: <A,HA>
+    Program setpop_prog;             // multi-set: <A^a, A^a> of every set's root block at setpop_off + 16 a
+    int64_t setpop_off = 0;
     std::vector<Program> rdm_prog;   // per leaf: gram walk + reduced density (slot rdm_slot[leaf])
     std::vector<int> rdm_slot;
     std::vector<Program> vac_prog;   // per leaf kept: vacuum projection, result vector slot vac_slot[leaf]
@@ -104,6 +117,8 @@ struct Plan {
 
 // Build the complete plan (layout + programs) for a tree and, if h != nullptr,
 // a Hamiltonian.  precision: TTN_FP64 (0) or TTN_MIXED (1).
+// With h->n_sets > 1 the plan is that of a multi-set state (nset = n_sets):
+// no expansion, ground-state, reduced-density or vacuum programs.
 std::string make_plan(const Tree& t, const Hamiltonian* h, int precision, Plan& plan);
 
 // Deterministic product state tensors (row-major per node) for leaf vectors.

@@ -19,13 +19,14 @@
 #define TTN_MAXD 8      // tensor modes per node (children + parent)
 #define TTN_KMAX 32     // maximal Krylov dimension
 #define TTN_MAXCHI 64   // largest bond / local dimension
+#define TTN_MAX_SETS 64 // largest set count of a multi-set state
 
 enum TtnOpType : int {
     TTN_OP_QR_DOWN = 1,      // A (a) = Q x_k R^T ;  bond buffer (b) <- R^T      (C[n_spf, m_shf])
     TTN_OP_QR_UP = 2,        // A (a) = Q x_last R;  bond buffer (b) <- R
     TTN_OP_ABSORB_CHILD = 3, // A (a) <- A x_last B^T   with B = bond buffer (b)
     TTN_OP_ABSORB_PARENT = 4,// A (a) <- B x_k A
-    TTN_OP_ENV = 5,          // out slots of entries += w * Q^dag (x_{j!=k} M_j) Q   (Q = a, keep mode k)
+    TTN_OP_ENV = 5,          // out slots of entries += w * Q^dag (x_{j!=k} M_j) P   (Q = a, P = c or a, keep mode k)
     TTN_OP_COMBO = 6,        // out slot of entries = sum w * M (slot[0] = -1: identity)
     TTN_OP_EVOLVE = 7,       // a <- exp(-i tau H) a, tau = tau_coef * dt, H = entries
     TTN_OP_DOT = 8,          // out scalar <- <a, H a> (ne > 0) or <a, a> (ne == 0)
@@ -54,6 +55,10 @@ struct TtnEntry {
     double wr, wi;          // complex weight
     int out;                // output slot (ENV, COMBO) or -1
     int slot[TTN_MAXD];     // factor slot per mode, -1 = identity
+    // Multi-set operators (EVOLVE / DOT with nset > 1): the entry reads set
+    // block `src` of its input and adds into set block `dst` of its output
+    // (the set pair |dst><src| of the term, paper Sec. II.A multi-set ansatz).
+    int src, dst;
 };
 
 struct TtnSlot {
@@ -69,11 +74,13 @@ struct TtnOp {
     int k;                  // mode argument
     int e0, ne;             // entry range
     int hermitian;          // EVOLVE: Lanczos (1) or Arnoldi (0)
-    int pad;
+    int nset;               // EVOLVE / DOT / PHASE: set blocks of tensor a (0 or 1: one)
     double tau_coef;        // EVOLVE
     void* a;                // main operand
     void* b;                // bond buffer / second operand / output tensor
     double* out;            // DOT / TRACE: complex scalar output (2 doubles)
+    // ENV: the ket tensor when it differs from the bra tensor a (multi-set
+    // cross-set environments), else null.
     // SPAWN: the child tensor, its index dimensions (children / physical, then
     // the bond), and the entry ranges of the child's up channels (e0/ne), of
     // the down channels of the bond built at this node (e1/ne1) and of the

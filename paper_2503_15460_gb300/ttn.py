@@ -59,6 +59,12 @@ _sig = {
     "ttn_set_state": ([_P, _C128, _I64], C.c_int),
     "ttn_set_product_state": ([_P, _C128, _I64], C.c_int),
     "ttn_set_sop_hamiltonian": ([_P, C.c_int, _C128, _I32, _I32, _C128, _I64, C.c_int], C.c_int),
+    "ttn_set_multiset_hamiltonian": ([_P, C.c_int, C.c_int, _C128, _I32, _I32, _C128, _I64, _I32, _I32, C.c_int],
+                                     C.c_int),
+    "ttn_set_multiset_state": ([_P, C.c_int, _C128, _I64], C.c_int),
+    "ttn_get_multiset_state": ([_P, C.c_int, _C128, _I64], C.c_int),
+    "ttn_set_populations": ([_P, _F64], C.c_int),
+    "ttn_n_sets": ([_P, C.POINTER(C.c_int)], C.c_int),
     "ttn_step": ([_P, C.c_double, C.c_int, C.POINTER(ttn_step_opts)], C.c_int),
     "ttn_step_batch": ([C.POINTER(_P), C.c_int, C.c_double, C.c_int, C.POINTER(ttn_step_opts)], C.c_int),
     "ttn_ground_state": ([_P, C.c_int, _F64], C.c_int),
@@ -200,6 +206,50 @@ def ttn_set_sop_hamiltonian(ctx, coeff, term_ptr, factor_leaf, factor_mats, fact
         off = np.zeros(1, np.int64)
     _check(_lib.ttn_set_sop_hamiltonian(ctx, len(coeff), coeff, term_ptr, factor_leaf, mats, off,
                                         int(bool(hermitian))), ctx)
+
+
+def ttn_set_multiset_hamiltonian(ctx, n_sets, coeff, term_ptr, factor_leaf, factor_mats, factor_mat_off, bra, ket,
+                                 hermitian):
+    coeff = np.ascontiguousarray(coeff, dtype=np.complex128)
+    term_ptr = np.ascontiguousarray(term_ptr, dtype=np.int32)
+    factor_leaf = np.ascontiguousarray(factor_leaf, dtype=np.int32)
+    if factor_leaf.size == 0:
+        factor_leaf = np.zeros(1, np.int32)
+    mats = np.ascontiguousarray(factor_mats, dtype=np.complex128)
+    if mats.size == 0:
+        mats = np.zeros(1, np.complex128)
+    off = np.ascontiguousarray(factor_mat_off, dtype=np.int64)
+    if off.size == 0:
+        off = np.zeros(1, np.int64)
+    bra = np.ascontiguousarray(bra, dtype=np.int32)
+    ket = np.ascontiguousarray(ket, dtype=np.int32)
+    _check(_lib.ttn_set_multiset_hamiltonian(ctx, int(n_sets), len(coeff), coeff, term_ptr, factor_leaf, mats, off,
+                                             bra, ket, int(bool(hermitian))), ctx)
+
+
+def ttn_set_multiset_state(ctx, tensor_sets):
+    """tensor_sets[alpha][z]: the tensor of set alpha at node z."""
+    flat, offs = _flatten([np.asarray(a, dtype=np.complex128).ravel() for As in tensor_sets for a in As])
+    _check(_lib.ttn_set_multiset_state(ctx, len(tensor_sets), flat, offs), ctx)
+
+
+def ttn_get_multiset_state(ctx, alpha, sizes):
+    out = np.zeros(int(sum(sizes)), dtype=np.complex128)
+    offs = np.zeros(len(sizes) + 1, dtype=np.int64)
+    _check(_lib.ttn_get_multiset_state(ctx, int(alpha), out, offs), ctx)
+    return [out[offs[i]:offs[i + 1]].copy() for i in range(len(sizes))]
+
+
+def ttn_n_sets(ctx):
+    n = C.c_int(0)
+    _check(_lib.ttn_n_sets(ctx, C.byref(n)), ctx)
+    return n.value
+
+
+def ttn_set_populations(ctx):
+    pops = np.zeros(ttn_n_sets(ctx), dtype=np.float64)
+    _check(_lib.ttn_set_populations(ctx, pops), ctx)
+    return pops
 
 
 def _opts(opts):
@@ -562,6 +612,26 @@ class Context:
     def set_hamiltonian(self, H):
         coeff, term_ptr, leaf, mats, off = H.to_csr()
         ttn_set_sop_hamiltonian(self.h, coeff, term_ptr, leaf, mats, off, H.hermitian)
+
+    def set_multiset_hamiltonian(self, H):
+        """H: workloads.MultiSetSOP (terms c_r |bra_r><ket_r| (x) factors)."""
+        coeff, term_ptr, leaf, mats, off, bra, ket = H.to_csr()
+        ttn_set_multiset_hamiltonian(self.h, H.n_sets, coeff, term_ptr, leaf, mats, off, bra, ket, H.hermitian)
+
+    def set_multiset_state(self, tensor_sets):
+        ttn_set_multiset_state(self.h, tensor_sets)
+
+    def n_sets(self):
+        return ttn_n_sets(self.h)
+
+    def set_populations(self):
+        return ttn_set_populations(self.h)
+
+    def get_multiset_state(self, alpha):
+        bond = self.bond_dims()
+        dims = [self.mode_dims(z, bond) for z in range(self.tree.n)]
+        flat = ttn_get_multiset_state(self.h, alpha, [int(np.prod(d)) for d in dims])
+        return [f.reshape(d) for f, d in zip(flat, dims)]
 
     def step(self, dt, nsteps=1, opts=None):
         ttn_step(self.h, dt, nsteps, opts)

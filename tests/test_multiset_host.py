@@ -1,0 +1,78 @@
+"""Host-side checks of the multi-set planner (paper Sec. II.A, multi-set
+ansatz), on host-resident contexts (no GPU): the channels crossing every
+bond are the distinct (bra set, ket set, part of a term on one side) with
+only same-set empty parts dropped as identities -- counted here by brute
+force -- and set counts that do not match are refused."""
+import numpy as np
+import pytest
+
+import workloads as W
+from tests.test_multiset_oracle import coupled_sop, small_tree
+
+
+def expected_dims(tree, H):
+    out = np.zeros(tree.n, dtype=np.int32)
+    for c in range(1, tree.n):
+        inside = set(tree.subtree_leaves(c))
+        ups, dns = set(), set()
+        for fs, a, b, coef in zip(H.factors, H.bra, H.ket, H.coeffs):
+            if coef == 0:
+                continue
+            fin = tuple(sorted((l, m) for (l, m) in fs if l in inside))
+            fout = tuple(sorted((l, m) for (l, m) in fs if l not in inside))
+            if a != b or fin:
+                ups.add((a, b, fin))
+            if a != b or fout:
+                dns.add((a, b, fout))
+        out[c] = len(ups) + len(dns)
+    return out
+
+
+def host_ctx(p_tree, H):
+    from paper_2503_15460_gb300 import ttn
+    c = ttn.Context(p_tree, ttn.TTN_FP64, on_host=True)
+    c.set_multiset_hamiltonian(H)
+    return c
+
+
+@pytest.mark.parametrize("which", ["random", "vibronic"])
+def test_multiset_channels_match_brute_force(which):
+    if which == "random":
+        t = small_tree(False)
+        H = coupled_sop(t, np.random.default_rng(3))
+    else:
+        p = W.multiset_vibronic_problem(n_states=3, n_modes=6, d=6, chi=4)
+        t, H = p.tree, p.H
+    c = host_ctx(t, H)
+    assert c.n_sets() == H.n_sets
+    np.testing.assert_array_equal(c.operator_dims(), expected_dims(t, H))
+    c.close()
+
+
+def test_set_count_mismatch_is_refused():
+    from paper_2503_15460_gb300 import ttn
+    t = small_tree(False)
+    H3 = coupled_sop(t, np.random.default_rng(3), S=3)
+    H2 = coupled_sop(t, np.random.default_rng(4), S=2)
+    c = host_ctx(t, H3)
+    with pytest.raises(ttn.TTNError):
+        c.set_multiset_hamiltonian(H2)             # a 3-set state cannot take a 2-set operator
+    with pytest.raises(ttn.TTNError):
+        c.set_multiset_state(W.multiset_product_state(t, [1.0, 0.0]))
+    with pytest.raises(ttn.TTNError):
+        c.set_state(W.product_state(t, {}))
+    c.set_multiset_state(W.multiset_product_state(t, [1.0, 0.0, 0.0]))
+    c.set_multiset_hamiltonian(H3)                 # same set count: accepted
+    c.close()
+
+
+def test_bad_set_index_is_refused():
+    from paper_2503_15460_gb300 import ttn
+    t = small_tree(False)
+    H = W.MultiSetSOP(n_sets=2)
+    H.add_set(0, 1, 0.5)
+    H.ket[0] = 2                                   # outside 0..1
+    c = ttn.Context(t, ttn.TTN_FP64, on_host=True)
+    with pytest.raises(ttn.TTNError):
+        c.set_multiset_hamiltonian(H)
+    c.close()

@@ -211,3 +211,26 @@ def test_full_bond_pin_catches_planted_mistakes(mistake):
     o.step(0.05, 12)
     ref = exact.propagate_eigh(exact.full_multiset_hamiltonian(t, H, dense=True), psi0, [0.6])[0]
     assert np.abs(o.full_state() - ref).max() > 1e-3
+
+
+def test_empty_set_start_is_ill_conditioned_occupied_is_not():
+    """Conditioning behind the GPU tests' choice of starts: a 1e-15
+    perturbation of the top tensors moves populations after 5 steps by more
+    than 1e-8 when two sets start empty (their functions come from QR of zero
+    or nearly zero matrices) and by less than 1e-12 when every set is
+    occupied."""
+    def moved(amps):
+        rng = np.random.default_rng(3)
+        t = small_tree(False)
+        H = coupled_sop(t, rng)
+        A = W.multiset_product_state(t, amps, [random_vecs(t, rng) for _ in range(3)])
+        Ap = [[a.copy() for a in As] for As in A]
+        r = np.random.default_rng(5)
+        for As in Ap:
+            As[0] = As[0] + 1e-15 * (r.normal(size=As[0].shape) + 1j * r.normal(size=As[0].shape))
+        o0, o1 = MultiSetTTN(t, H, A), MultiSetTTN(t, H, Ap)
+        o0.step(0.05, 5)
+        o1.step(0.05, 5)
+        return np.abs(o0.set_populations() - o1.set_populations()).max()
+    assert moved([1.0, 0.0, 0.0]) > 1e-8
+    assert moved([0.6, 0.48j, 0.64]) < 1e-12
