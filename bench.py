@@ -80,6 +80,11 @@ def workload_name(batch, workload="vibronic"):
         return (f"HEOM spin-boson as a TTN: 16 exponentials (Drude-Lorentz + 15 Matsubara), depth 10 "
                 f"(32 modes of dim 11), system leaf dim 4, balanced binary tree (65 nodes), chi 24, Arnoldi; "
                 f"batch of {batch} instances sweeping the reorganisation energy lambda, dt={WORKLOAD_DT[workload]}")
+    if workload == "multiset":
+        return (f"multi-set linear vibronic model (the sets are {MULTISET_SHAPE['n_states']} electronic states, "
+                f"one TTN each): {MULTISET_SHAPE['n_modes']} modes of dim {MULTISET_SHAPE['d']}, balanced binary "
+                f"tree, bonds {MULTISET_SHAPE['chi']}, set 0 occupied at t = 0; batch of {batch} seeded instances, "
+                f"dt={WORKLOAD_DT[workload]}")
     if workload == "spinboson300":
         return (f"spin-boson, 1 spin + 300 Ohmic modes (wc 5, orthogonal-polynomial bath on [0, 50]), d 20, "
                 f"balanced binary tree (601 nodes), fixed chi 8; batch of {batch} instances sweeping alpha "
@@ -88,7 +93,8 @@ def workload_name(batch, workload="vibronic"):
             f"local dims 10..30), batch of {batch} seeded instances, dt={DT}")
 
 
-WORKLOAD_DT = {"vibronic": DT, "heom": 0.015, "spinboson300": 0.01}
+WORKLOAD_DT = {"vibronic": DT, "heom": 0.015, "spinboson300": 0.01, "multiset": 0.1}
+MULTISET_SHAPE = {"n_states": 4, "n_modes": 16, "d": 8, "chi": 8}
 
 
 def rank_seed0(batch, rank):
@@ -120,6 +126,9 @@ def make_problems(batch, seed0, workload="vibronic"):
     import workloads as W
     if workload == "heom":
         return [W.config_c4(lam=0.05 + 0.0005 * (seed0 - 2 + i)) for i in range(batch)]
+    if workload == "multiset":
+        return [W.multiset_vibronic_problem(seed=seed0 + i, dt=WORKLOAD_DT["multiset"], **MULTISET_SHAPE)
+                for i in range(batch)]
     if workload == "spinboson300":
         # alpha only scales the couplings (g ~ sqrt(alpha)): discretise once
         import dataclasses
@@ -188,8 +197,18 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # our implementation
 # ---------------------------------------------------------------------------
+def observed_populations(ctx, p):
+    """Site populations of the observed leaves, or the set populations of a
+    multi-set state."""
+    import workloads as W
+    if isinstance(p, W.MultiSetProblem):
+        return ctx.set_populations()
+    return np.concatenate(ctx.populations(p.obs_leaves))
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
+    import workloads as W
     torch.cuda.set_device(local_rank)
     from paper_2503_15460_gb300 import ttn
     ttn.ttn_set_device(local_rank)
@@ -203,8 +222,12 @@ def run_ours(args, rank, world, local_rank):
         for p in (probs if subset is None else subset):
             c = ttn.Context(p.tree, precision)
             ttn.ttn_set_stream(c.h, stream.cuda_stream)
-            c.set_state(p.tensors)
-            c.set_hamiltonian(p.H)
+            if isinstance(p, W.MultiSetProblem):
+                c.set_multiset_hamiltonian(p.H)
+                c.set_multiset_state(p.tensors)
+            else:
+                c.set_state(p.tensors)
+                c.set_hamiltonian(p.H)
             out.append(c)
         return out
 
@@ -276,15 +299,15 @@ def run_ours(args, rank, world, local_rank):
         ttn.ttn_step_batch([c.h for c in cref], DT, horizon)
         err = 0.0
         for a, b, p in zip(ctxs[:nchk], cref, probs[:nchk]):
-            pa = np.concatenate(a.populations(p.obs_leaves))
-            pb = np.concatenate(b.populations(p.obs_leaves))
+            pa, pb = observed_populations(a, p), observed_populations(b, p)
             err = max(err, float(np.abs(pa - pb).max()))
         for c in cref:
             c.close()
         fp64["pop_err_mixed_vs_fp64"] = err
         fp64["pop_err_steps"] = horizon
         fp64["pop_err_instances"] = nchk
-        fp64["pop_err_note"] = ("max |population| difference over all leaves after the warm-up and timed steps of "
+        fp64["pop_err_note"] = ("max |population| difference over all leaves (multi-set: over the sets) after the "
+                                "warm-up and timed steps of "
                                 "the benchmarked mixed batch, against complex128 from the same initial states")
 
     # ---- end to end through the public API (host buffers) --------------------
@@ -654,7 +677,7 @@ def main():
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu", dest="cpu", action="store_false")
     ap.add_argument("--workload", default="vibronic", choices=sorted(WORKLOAD_DT),
-                    help="vibronic (the headline), heom or spinboson300 (batched parameter sweeps)")
+                    help="vibronic (the headline), heom, spinboson300 or multiset (batched parameter sweeps)")
     ap.add_argument("--serve", action="store_true", help="run the serving stream instead (separate JSON line)")
     ap.add_argument("--accuracy", action="store_true",
                     help="mixed against complex128 over the workload's horizon instead (separate JSON line)")

@@ -398,9 +398,12 @@ ttn_status ttn_tuning(const ttn_ctx* ctx, int* blocks, unsigned char* variants, 
  * whose vertices are their distinct inside and outside parts (a term is
  * summed into the channel of its inside part when that is in the cover,
  * else into the channel of its outside part); out[0] = 0.  For a multi-set
- * operator (ttn_set_multiset_hamiltonian): the number of distinct
- * (bra set, ket set, inside part) plus (bra set, ket set, outside part)
- * channels, less the same-set empty ones (identities).  Works on
+ * operator (ttn_set_multiset_hamiltonian): per set, one pre-summed channel
+ * for its terms acting only inside the subtree and one for those acting
+ * only outside, plus the distinct (bra set, ket set, inside part) and
+ * (bra set, ket set, outside part) channels of the same-set terms acting on
+ * both sides and of every set-coupling term (an empty part of a coupling
+ * is the overlap of the two sets' functions there).  Works on
  * host-resident contexts (no device work).  TTN_E_STATE without a
  * Hamiltonian. */
 ttn_status ttn_operator_dims(const ttn_ctx* ctx, int* out);

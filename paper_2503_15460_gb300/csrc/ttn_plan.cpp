@@ -1098,8 +1098,12 @@ struct Builder {
 // a bond) and stands for that part's matrix element between the bra set's
 // and the ket set's functions there.  Only a same-set channel with an empty
 // part is the identity; for a != b an empty part is the overlap of the two
-// sets' functions, a real matrix.  No further grouping: terms with the same
-// set pair and the same part share the channel.
+// sets' functions, a real matrix.  Per set, the terms acting only inside a
+// subtree are pre-summed into one local channel of its bond (LOC), those
+// acting only outside into one local mean-field channel (DLOC), and a
+// leaf's own terms into one constant matrix (the single-set planner's local
+// channels); terms crossing a bond and terms coupling two sets keep a
+// channel per (set pair, part).
 // ---------------------------------------------------------------------------
 struct MsBuilder {
     const Tree& t;
@@ -1107,7 +1111,8 @@ struct MsBuilder {
     Plan& p;
     const int S;
     using CKey = std::tuple<int, int, Key>;
-    struct Def { int up; int c; CKey key; int slot; };
+    enum { D_DN = 0, D_UP = 1, D_LOC = 2, D_DLOC = 3 };
+    struct Def { int up; int c; CKey key; int slot; };   // up: one of D_*
     std::vector<std::map<CKey, int>> up_ch, dn_ch;       // per bond (child node)
     std::vector<Def> todo;
     std::map<std::pair<int, int>, int> phys;             // (leaf, matrix id) -> constant slot
@@ -1117,8 +1122,73 @@ struct MsBuilder {
     std::vector<std::pair<int, int>> heff_rng, bond_rng;
     std::vector<std::map<std::pair<int, int>, std::pair<int, int>>> up_rng, dn_rng;
 
+    // local channels per (node, set): slot, or -1 before creation; existence
+    std::vector<std::vector<int>> loc_slot, dloc_slot;
+    std::vector<std::vector<char>> has_loc, has_dloc;
+    std::map<std::pair<int, int>, int> pl;               // (leaf, set) -> constant slot of its own terms
+
     MsBuilder(const Tree& t_, const Hamiltonian& h_, Plan& p_) : t(t_), h(h_), p(p_), S(h_.n_sets) {
         up_ch.resize(t.n); dn_ch.resize(t.n); up_env.resize(t.n); dn_env.resize(t.n);
+        loc_slot.assign(t.n, std::vector<int>(S, -1));
+        dloc_slot.assign(t.n, std::vector<int>(S, -1));
+        has_loc.assign(t.n, std::vector<char>(S, 0));
+        has_dloc.assign(t.n, std::vector<char>(S, 0));
+        for (size_t r = 0; r < h.terms.size(); ++r) {
+            if (!diag(r)) continue;
+            for (int c = 1; c < t.n; ++c) {
+                const bool in = !restrict_to(h.terms[r], c, true).empty(), out = !restrict_to(h.terms[r], c, false).empty();
+                if (in && !out) has_loc[c][h.bra[r]] = 1;
+                if (out && !in) has_dloc[c][h.bra[r]] = 1;
+            }
+        }
+    }
+    // a same-set term acting somewhere (pre-summed where it is local)
+    bool diag(size_t r) const { return h.bra[r] == h.ket[r] && !h.terms[r].empty(); }
+    // mode of node z holding leaf l: its child index, 0 for a leaf's own factor, D-1 outside
+    int mode_of(int z, int l) const {
+        const int D = (int)t.dims[z].size();
+        if (!t.in_sub(l, z)) return D - 1;
+        if (t.leaf(z)) return 0;
+        for (size_t k = 0; k < t.ch[z].size(); ++k)
+            if (t.in_sub(l, t.ch[z][k])) return (int)k;
+        return -1;
+    }
+    std::set<int> touched(int z, const Key& key) const {
+        std::set<int> m;
+        for (auto& f : key) m.insert(mode_of(z, f.first));
+        return m;
+    }
+    int get_loc(int c, int a) {
+        if (!has_loc[c][a]) return -1;
+        if (loc_slot[c][a] < 0) {
+            loc_slot[c][a] = new_slot(t.bond[c], t.bond[c]);
+            todo.push_back({D_LOC, c, CKey{a, a, {}}, loc_slot[c][a]});
+        }
+        return loc_slot[c][a];
+    }
+    int get_dloc(int c, int a) {
+        if (c == 0 || !has_dloc[c][a]) return -1;
+        if (dloc_slot[c][a] < 0) {
+            dloc_slot[c][a] = new_slot(t.bond[c], t.bond[c]);
+            todo.push_back({D_DLOC, c, CKey{a, a, {}}, dloc_slot[c][a]});
+        }
+        return dloc_slot[c][a];
+    }
+    // sum of c_r M_r over set a's terms whose only factor is on leaf l (constant)
+    int get_pl(int l, int a) {
+        auto it = pl.find({l, a});
+        if (it != pl.end()) return it->second;
+        const int d = t.phys[l];
+        std::vector<cplx> sum((size_t)d * d, 0.0);
+        for (size_t r = 0; r < h.terms.size(); ++r) {
+            if (!diag(r) || h.bra[r] != a || h.terms[r].size() != 1 || h.terms[r][0].first != l) continue;
+            const auto& M = h.mats[h.terms[r][0].second];
+            for (int i = 0; i < d * d; ++i) sum[i] += h.coeff[r] * M[i];
+        }
+        int id = new_slot(d, d);
+        p.slots[id].constant = true;
+        p.slots[id].data = sum;
+        return pl[{l, a}] = id;
     }
     int new_slot(int rows, int cols) {
         SlotInfo s; s.rows = rows; s.cols = cols;
@@ -1148,7 +1218,7 @@ struct MsBuilder {
         if (it != m.end()) return it->second;
         int s = new_slot(t.bond[c], t.bond[c]);
         m[key] = s;
-        todo.push_back({up ? 1 : 0, c, key, s});
+        todo.push_back({up ? D_UP : D_DN, c, key, s});
         return s;
     }
     // slot list of a term part `key` (the whole term, or its part on one
@@ -1177,7 +1247,9 @@ struct MsBuilder {
         Proto e;
         e.w = 1.0;
         e.out = q.slot;
-        if (q.up) {
+        if (q.up == D_LOC) { define_loc(q.c, a, q.slot); return; }
+        if (q.up == D_DLOC) { define_dloc(q.c, a, q.slot); return; }
+        if (q.up == D_UP) {
             // at node c, every mode but the parent's
             e.slot = mode_slots(q.c, a, b, part, (int)t.dims[q.c].size() - 1);
             up_env[q.c][{a, b}].push_back(e);
@@ -1188,6 +1260,72 @@ struct MsBuilder {
             e.slot = mode_slots(z, a, b, part, k);
             dn_env[q.c][{a, b}].push_back(e);
         }
+    }
+    // LOC(c, a) = sum over set a's terms acting only inside c of c_r h_r(c),
+    // built at node c: the children's LOC on their modes, the terms spanning
+    // two or more children term by term (a leaf: its constant sum).
+    void define_loc(int c, int a, int slot) {
+        std::vector<Proto> es;
+        const int D = (int)t.dims[c].size();
+        Proto e;
+        e.w = 1.0; e.out = slot; e.slot.assign(D, -1);
+        if (t.leaf(c)) {
+            e.slot[0] = get_pl(c, a);
+            es.push_back(e);
+        } else {
+            for (size_t k = 0; k < t.ch[c].size(); ++k) {
+                const int s = get_loc(t.ch[c][k], a);
+                if (s < 0) continue;
+                Proto f = e;
+                f.slot[k] = s;
+                es.push_back(f);
+            }
+            for (size_t r = 0; r < h.terms.size(); ++r) {
+                if (!diag(r) || h.bra[r] != a || !restrict_to(h.terms[r], c, false).empty()) continue;
+                if (touched(c, h.terms[r]).size() < 2) continue;
+                Proto f;
+                f.w = h.coeff[r]; f.out = slot;
+                f.slot = mode_slots(c, a, a, h.terms[r], D - 1);
+                es.push_back(f);
+            }
+        }
+        auto& dst = up_env[c][{a, a}];
+        dst.insert(dst.end(), es.begin(), es.end());
+    }
+    // DLOC(c, a) = sum over set a's terms acting only outside c of c_r H_r(c),
+    // built at the parent z keeping c's mode: the siblings' LOC, z's DLOC and
+    // the terms spanning two or more of those modes term by term.
+    void define_dloc(int c, int a, int slot) {
+        std::vector<Proto> es;
+        const int z = t.parent[c];
+        const int k = (int)(std::find(t.ch[z].begin(), t.ch[z].end(), c) - t.ch[z].begin());
+        const int D = (int)t.dims[z].size();
+        Proto e;
+        e.w = 1.0; e.out = slot; e.slot.assign(D, -1);
+        for (size_t j = 0; j < t.ch[z].size(); ++j) {
+            if ((int)j == k) continue;
+            const int s = get_loc(t.ch[z][j], a);
+            if (s < 0) continue;
+            Proto f = e;
+            f.slot[j] = s;
+            es.push_back(f);
+        }
+        const int sd = get_dloc(z, a);
+        if (sd >= 0) {
+            Proto f = e;
+            f.slot[D - 1] = sd;
+            es.push_back(f);
+        }
+        for (size_t r = 0; r < h.terms.size(); ++r) {
+            if (!diag(r) || h.bra[r] != a || !restrict_to(h.terms[r], c, true).empty()) continue;
+            if (touched(z, h.terms[r]).size() < 2) continue;
+            Proto f;
+            f.w = h.coeff[r]; f.out = slot;
+            f.slot = mode_slots(z, a, a, h.terms[r], k);
+            es.push_back(f);
+        }
+        auto& dst = dn_env[c][{a, a}];
+        dst.insert(dst.end(), es.begin(), es.end());
     }
     void close() {
         for (size_t i = 0; i < todo.size(); ++i) {
@@ -1241,18 +1379,56 @@ struct MsBuilder {
         const int n = t.n, R = (int)h.terms.size();
         std::vector<std::vector<Proto>> heff(n), bond(n);
         p.op_bond_dim.assign(n, 0);
+        std::vector<cplx> konst(S, 0.0);                 // same-set constants
+        for (int r = 0; r < R; ++r)
+            if (h.bra[r] == h.ket[r] && h.terms[r].empty()) konst[h.bra[r]] += h.coeff[r];
+        auto one = [&](int dst, int src, cplx w, std::vector<int> sl) {
+            Proto e;
+            e.w = w; e.out = -1; e.dst = dst; e.src = src; e.slot = std::move(sl);
+            return e;
+        };
         for (int z = 0; z < n; ++z) {
-            for (int r = 0; r < R; ++r) {
-                Proto e;
-                e.w = h.coeff[r]; e.out = -1; e.dst = h.bra[r]; e.src = h.ket[r];
-                e.slot = mode_slots(z, h.bra[r], h.ket[r], h.terms[r], -1);
-                heff[z].push_back(e);
+            const int D = (int)t.dims[z].size();
+            for (int a = 0; a < S; ++a) {
+                // local sums: the children's (a leaf's own terms), the outside's, constants
+                if (t.leaf(z)) {
+                    if (z > 0 && has_loc[z][a]) {
+                        std::vector<int> sl(D, -1);
+                        sl[0] = get_pl(z, a);
+                        heff[z].push_back(one(a, a, 1.0, sl));
+                    }
+                } else {
+                    for (size_t k = 0; k < t.ch[z].size(); ++k) {
+                        const int s = get_loc(t.ch[z][k], a);
+                        if (s < 0) continue;
+                        std::vector<int> sl(D, -1);
+                        sl[k] = s;
+                        heff[z].push_back(one(a, a, 1.0, sl));
+                    }
+                }
+                const int sd = get_dloc(z, a);
+                if (sd >= 0) {
+                    std::vector<int> sl(D, -1);
+                    sl[D - 1] = sd;
+                    heff[z].push_back(one(a, a, 1.0, sl));
+                }
+                if (konst[a] != cplx(0.0)) heff[z].push_back(one(a, a, konst[a], std::vector<int>(D, -1)));
                 if (z == 0) continue;
-                Proto f;
-                f.w = h.coeff[r]; f.out = -1; f.dst = h.bra[r]; f.src = h.ket[r];
-                f.slot = {chan(true, z, h.bra[r], h.ket[r], restrict_to(h.terms[r], z, true)),
-                          chan(false, z, h.bra[r], h.ket[r], restrict_to(h.terms[r], z, false))};
-                bond[z].push_back(f);
+                const int sl_ = get_loc(z, a), sdl = get_dloc(z, a);
+                if (sl_ >= 0) bond[z].push_back(one(a, a, 1.0, {sl_, -1}));
+                if (sdl >= 0) bond[z].push_back(one(a, a, 1.0, {-1, sdl}));
+                if (konst[a] != cplx(0.0)) bond[z].push_back(one(a, a, konst[a], {-1, -1}));
+            }
+            for (int r = 0; r < R; ++r) {
+                const int a = h.bra[r], b = h.ket[r];
+                if (a == b && h.terms[r].empty()) continue;          // constants: above
+                // same-set terms on one mode of z are in the local sums
+                if (a != b || touched(z, h.terms[r]).size() >= 2)
+                    heff[z].push_back(one(a, b, h.coeff[r], mode_slots(z, a, b, h.terms[r], -1)));
+                if (z == 0) continue;
+                const Key in = restrict_to(h.terms[r], z, true), out = restrict_to(h.terms[r], z, false);
+                if (a == b && (in.empty() || out.empty())) continue;  // local: above
+                bond[z].push_back(one(a, b, h.coeff[r], {chan(true, z, a, b, in), chan(false, z, a, b, out)}));
             }
         }
         close();
@@ -1262,7 +1438,9 @@ struct MsBuilder {
             heff_rng[z] = push(heff[z]);
             if (z == 0) continue;
             bond_rng[z] = push(bond[z]);
-            p.op_bond_dim[z] = (int)(up_ch[z].size() + dn_ch[z].size());
+            int nloc = 0;
+            for (int a = 0; a < S; ++a) nloc += (loc_slot[z][a] >= 0) + (dloc_slot[z][a] >= 0);
+            p.op_bond_dim[z] = (int)(up_ch[z].size() + dn_ch[z].size()) + nloc;
             for (auto& kv : up_env[z]) up_rng[z][kv.first] = push(kv.second);
             for (auto& kv : dn_env[z]) dn_rng[z][kv.first] = push(kv.second);
         }

@@ -1,8 +1,11 @@
 """Host-side checks of the multi-set planner (paper Sec. II.A, multi-set
 ansatz), on host-resident contexts (no GPU): the channels crossing every
-bond are the distinct (bra set, ket set, part of a term on one side) with
-only same-set empty parts dropped as identities -- counted here by brute
-force -- and set counts that do not match are refused."""
+bond -- counted here by brute force -- are, per set, one pre-summed local
+channel for its terms acting only inside the subtree and one for those
+acting only outside, plus one channel per distinct (bra set, ket set, part
+of a term on that side) for the same-set terms acting on both sides and
+for every term coupling two sets (whose empty parts are overlaps, not
+identities); set counts that do not match are refused."""
 import numpy as np
 import pytest
 
@@ -14,17 +17,22 @@ def expected_dims(tree, H):
     out = np.zeros(tree.n, dtype=np.int32)
     for c in range(1, tree.n):
         inside = set(tree.subtree_leaves(c))
-        ups, dns = set(), set()
+        ups, dns, loc, dloc = set(), set(), set(), set()
         for fs, a, b, coef in zip(H.factors, H.bra, H.ket, H.coeffs):
             if coef == 0:
                 continue
             fin = tuple(sorted((l, m) for (l, m) in fs if l in inside))
             fout = tuple(sorted((l, m) for (l, m) in fs if l not in inside))
-            if a != b or fin:
-                ups.add((a, b, fin))
-            if a != b or fout:
-                dns.add((a, b, fout))
-        out[c] = len(ups) + len(dns)
+            if a == b:
+                if fin and not fout:
+                    loc.add(a)
+                elif fout and not fin:
+                    dloc.add(a)
+                elif fin and fout:
+                    ups.add((a, b, fin)); dns.add((a, b, fout))
+            else:
+                ups.add((a, b, fin)); dns.add((a, b, fout))
+        out[c] = len(loc) + len(dloc) + len(ups) + len(dns)
     return out
 
 
