@@ -83,7 +83,8 @@ def workload_name(batch, workload="vibronic"):
     if workload == "multiset":
         return (f"multi-set linear vibronic model (the sets are {MULTISET_SHAPE['n_states']} electronic states, "
                 f"one TTN each): {MULTISET_SHAPE['n_modes']} modes of dim {MULTISET_SHAPE['d']}, balanced binary "
-                f"tree, bonds {MULTISET_SHAPE['chi']}, set 0 occupied at t = 0; batch of {batch} seeded instances, "
+                f"tree, bonds {MULTISET_SHAPE['chi']}, every set occupied at t = 0 (amplitudes {MULTISET_AMPS}, "
+                f"normalised); batch of {batch} seeded instances, "
                 f"dt={WORKLOAD_DT[workload]}")
     if workload == "spinboson300":
         return (f"spin-boson, 1 spin + 300 Ohmic modes (wc 5, orthogonal-polynomial bath on [0, 50]), d 20, "
@@ -95,6 +96,10 @@ def workload_name(batch, workload="vibronic"):
 
 WORKLOAD_DT = {"vibronic": DT, "heom": 0.015, "spinboson300": 0.01, "multiset": 0.1}
 MULTISET_SHAPE = {"n_states": 4, "n_modes": 16, "d": 8, "chi": 8}
+# every set occupied at t = 0 (a superposition): a start with empty sets is
+# ill-conditioned at truncated bonds, so the mixed-vs-complex128 check would
+# measure the conditioning, not the arithmetic
+MULTISET_AMPS = (0.85, 0.3, 0.3, 0.3)
 
 
 def rank_seed0(batch, rank):
@@ -127,7 +132,8 @@ def make_problems(batch, seed0, workload="vibronic"):
     if workload == "heom":
         return [W.config_c4(lam=0.05 + 0.0005 * (seed0 - 2 + i)) for i in range(batch)]
     if workload == "multiset":
-        return [W.multiset_vibronic_problem(seed=seed0 + i, dt=WORKLOAD_DT["multiset"], **MULTISET_SHAPE)
+        return [W.multiset_vibronic_problem(seed=seed0 + i, dt=WORKLOAD_DT["multiset"], amps=MULTISET_AMPS,
+                                            **MULTISET_SHAPE)
                 for i in range(batch)]
     if workload == "spinboson300":
         # alpha only scales the couplings (g ~ sqrt(alpha)): discretise once

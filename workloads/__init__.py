@@ -646,7 +646,7 @@ class MultiSetProblem:
 
 def multiset_vibronic_problem(n_states: int = 3, n_modes: int = 6, d: int = 6, chi: int = 4,
                               seed: int = 7, dt: float = 0.1, nsteps: int = 50,
-                              n_coupling_modes: int = 2) -> MultiSetProblem:
+                              n_coupling_modes: int = 2, amps=None) -> MultiSetProblem:
     """Linear vibronic coupling model in the multi-set form (the electronic
     states are the sets, the modes the environment tree; the form of the
     exciton models of paper Sec. IV.B), seeded:
@@ -655,7 +655,8 @@ def multiset_vibronic_problem(n_states: int = 3, n_modes: int = 6, d: int = 6, c
     with w ~ U[0.05, 0.5], E_s ~ N(0, 0.05^2), kappa ~ N(0, 0.05^2),
     J ~ N(0, 0.03^2), lam ~ N(0, 0.03^2), Q = (a + a^+)/sqrt(2), on a balanced
     binary tree over the modes (leaf bonds min(chi, d), interior bonds chi).
-    Initial state: set 0 times the vibrational vacuum, the other sets empty."""
+    Initial state: sum_s amps[s] |s> x vibrational vacuum; default set 0
+    alone (the other sets empty)."""
     rng = np.random.default_rng(seed)
     omega = rng.uniform(0.05, 0.5, n_modes)
     E = rng.normal(0.0, 0.05, n_states)
@@ -686,7 +687,10 @@ def multiset_vibronic_problem(n_states: int = 3, n_modes: int = 6, d: int = 6, c
             H.add_set(s_, s2, J[a, b])
             for j, i in enumerate(cm):
                 H.add_set(s_, s2, lam[j, a, b], (modes[i], Q))
-    A = multiset_product_state(t, [1.0] + [0.0] * (n_states - 1))
+    if amps is None:
+        amps = [1.0] + [0.0] * (n_states - 1)
+    amps = np.asarray(amps, dtype=np.complex128)
+    A = multiset_product_state(t, list(amps / np.linalg.norm(amps)))
     return MultiSetProblem(f"multiset_vibronic_{n_states}x{n_modes}_d{d}_chi{chi}_seed{seed}", t, H, A,
                            dt, nsteps, {"modes": modes, "coupling_modes": cm})
 
