@@ -188,3 +188,52 @@ def test_multiset_refuses_single_set_calls(gpu_lib):
     c.step(p.dt, 2)                                   # still usable
     assert abs(c.set_populations().sum() - 1.0) < 1e-11
     c.close()
+
+
+@pytest.mark.parametrize("blocks", [4])
+def test_multiset_on_a_cluster_team_matches_oracle(gpu_lib, blocks):
+    """The set blocks through the cluster team (row-split QR, dealt-out Gram
+    tiles, DSMEM reductions) give the oracle's trajectory too."""
+    name, t, H, A, dt = list(problems())[1]
+    ref = MultiSetTTN(t, H, A)
+    c = ctx_for(gpu_lib, t, H, A, gpu_lib.TTN_FP64)
+    c.set_cluster(blocks)
+    for _ in range(2):
+        ref.step(dt, 5)
+        c.step(dt, 5)
+        np.testing.assert_allclose(gpu_full(c, t, H.n_sets), ref.full_state(), atol=FP64_TOL, err_msg=name)
+    c.close()
+
+
+def test_multiset_requests_through_the_server(gpu_lib):
+    """Multi-set contexts served beside single-set ones give the tensors of
+    the same contexts run alone with ttn_step."""
+    ms = [W.multiset_vibronic_problem(n_states=3, n_modes=5, d=5, chi=3, seed=s, amps=OCCUPIED) for s in (1, 2)]
+    ss = [W.vibronic_balanced_problem(6, 5, 3, seed=s, nsteps=6) for s in (3, 4)]
+    steps = 6
+
+    def fresh():
+        out = [ctx_for(gpu_lib, p.tree, p.H, p.tensors, gpu_lib.TTN_MIXED) for p in ms]
+        for p in ss:
+            c = gpu_lib.Context(p.tree, gpu_lib.TTN_MIXED)
+            c.set_state(p.tensors)
+            c.set_hamiltonian(p.H)
+            out.append(c)
+        return out
+
+    alone = fresh()
+    for c, p in zip(alone, ms + ss):
+        c.step(p.dt, steps)
+    served = fresh()
+    srv = gpu_lib.Server(gpu_lib.TTN_MIXED)
+    for c, p in zip(served, ms + ss):
+        srv.submit(c, p.dt, steps)
+    srv.drain()
+    for a, b, p in zip(alone[:2], served[:2], ms):
+        np.testing.assert_array_equal(gpu_full(a, p.tree, 3), gpu_full(b, p.tree, 3))
+    for a, b in zip(alone[2:], served[2:]):
+        for x, y in zip(a.get_state(), b.get_state()):
+            np.testing.assert_array_equal(x, y)
+    srv.close()
+    for c in alone + served:
+        c.close()
