@@ -400,10 +400,13 @@ ttn_status ttn_tuning(const ttn_ctx* ctx, int* blocks, unsigned char* variants, 
  * else into the channel of its outside part); out[0] = 0.  For a multi-set
  * operator (ttn_set_multiset_hamiltonian): per set, one pre-summed channel
  * for its terms acting only inside the subtree and one for those acting
- * only outside, plus the distinct (bra set, ket set, inside part) and
- * (bra set, ket set, outside part) channels of the same-set terms acting on
- * both sides and of every set-coupling term (an empty part of a coupling
- * is the overlap of the two sets' functions there).  Works on
+ * only outside; for the terms crossing the bond (same-set terms acting on
+ * both sides, every set-coupling term -- an empty part of a coupling is
+ * the overlap of the two sets' functions there), per set pair, one channel
+ * per distinct inside part and one summed mean-field channel per distinct
+ * inside part where the pair has fewer distinct inside than outside parts
+ * there, else one channel per distinct inside and per distinct outside
+ * part.  Works on
  * host-resident contexts (no device work).  TTN_E_STATE without a
  * Hamiltonian. */
 ttn_status ttn_operator_dims(const ttn_ctx* ctx, int* out);

@@ -1111,9 +1111,14 @@ struct MsBuilder {
     Plan& p;
     const int S;
     using CKey = std::tuple<int, int, Key>;
-    enum { D_DN = 0, D_UP = 1, D_LOC = 2, D_DLOC = 3 };
+    enum { D_DN = 0, D_UP = 1, D_LOC = 2, D_DLOC = 3, D_DG = 4 };
     struct Def { int up; int c; CKey key; int slot; };   // up: one of D_*
     std::vector<std::map<CKey, int>> up_ch, dn_ch;       // per bond (child node)
+    // grouped mean-field channels per bond: key (a, b, inside part); the
+    // set pairs whose crossing terms a bond groups that way (those with fewer
+    // distinct inside than outside parts there)
+    std::vector<std::map<CKey, int>> dg_ch;
+    std::vector<std::set<std::pair<int, int>>> dg_pair;
     std::vector<Def> todo;
     std::map<std::pair<int, int>, int> phys;             // (leaf, matrix id) -> constant slot
     // ENV entries per bond and set pair: built at the child (up) or at the
@@ -1128,11 +1133,23 @@ struct MsBuilder {
     std::map<std::pair<int, int>, int> pl;               // (leaf, set) -> constant slot of its own terms
 
     MsBuilder(const Tree& t_, const Hamiltonian& h_, Plan& p_) : t(t_), h(h_), p(p_), S(h_.n_sets) {
-        up_ch.resize(t.n); dn_ch.resize(t.n); up_env.resize(t.n); dn_env.resize(t.n);
+        up_ch.resize(t.n); dn_ch.resize(t.n); dg_ch.resize(t.n); up_env.resize(t.n); dn_env.resize(t.n);
         loc_slot.assign(t.n, std::vector<int>(S, -1));
         dloc_slot.assign(t.n, std::vector<int>(S, -1));
         has_loc.assign(t.n, std::vector<char>(S, 0));
         has_dloc.assign(t.n, std::vector<char>(S, 0));
+        dg_pair.assign(t.n, {});
+        for (int c = 1; c < t.n; ++c) {
+            std::map<std::pair<int, int>, std::pair<std::set<Key>, std::set<Key>>> parts;
+            for (size_t r = 0; r < h.terms.size(); ++r) {
+                if (!crossing(r, c)) continue;
+                auto& pr = parts[{h.bra[r], h.ket[r]}];
+                pr.first.insert(restrict_to(h.terms[r], c, true));
+                pr.second.insert(restrict_to(h.terms[r], c, false));
+            }
+            for (auto& kv : parts)
+                if (kv.second.first.size() < kv.second.second.size()) dg_pair[c].insert(kv.first);
+        }
         for (size_t r = 0; r < h.terms.size(); ++r) {
             if (!diag(r)) continue;
             for (int c = 1; c < t.n; ++c) {
@@ -1157,6 +1174,59 @@ struct MsBuilder {
         std::set<int> m;
         for (auto& f : key) m.insert(mode_of(z, f.first));
         return m;
+    }
+    // term r crosses bond c: a set coupling always (overlaps on both sides),
+    // a same-set term when it acts on both sides
+    bool crossing(size_t r, int c) const {
+        if (h.bra[r] != h.ket[r]) return true;
+        return !restrict_to(h.terms[r], c, true).empty() && !restrict_to(h.terms[r], c, false).empty();
+    }
+    // DG(c, a, b, in) = sum over the terms of set pair (a, b) crossing bond c
+    // with inside part `in` of c_r H_r(c) (their mean fields, weighted)
+    int get_dg(int c, int a, int b, const Key& in) {
+        CKey key{a, b, in};
+        auto it = dg_ch[c].find(key);
+        if (it != dg_ch[c].end()) return it->second;
+        int s = new_slot(t.bond[c], t.bond[c]);
+        dg_ch[c][key] = s;
+        todo.push_back({D_DG, c, key, s});
+        return s;
+    }
+    // Entry of term r at node z (mode `skip` kept, -1: none; `out`: ENV
+    // output slot or -1).  A term that crosses z's own bond enters through
+    // z's grouped channel for its inside part -- weight 1, once per (set
+    // pair, inside part) in `seen` -- else term by term.
+    void term_at(int z, size_t r, int skip, int out, std::set<CKey>& seen, std::vector<Proto>& es) {
+        const int a = h.bra[r], b = h.ket[r];
+        Proto e;
+        e.out = out; e.dst = a; e.src = b;
+        if (z > 0 && crossing(r, z) && dg_pair[z].count({a, b})) {
+            const Key in = restrict_to(h.terms[r], z, true);
+            if (!seen.insert(CKey{a, b, in}).second) return;
+            const int D = (int)t.dims[z].size();
+            e.w = 1.0;
+            e.slot = mode_slots(z, a, b, in, skip, false);
+            e.slot[D - 1] = get_dg(z, a, b, in);
+            es.push_back(e);
+            return;
+        }
+        e.w = h.coeff[r];
+        e.slot = mode_slots(z, a, b, h.terms[r], skip);
+        es.push_back(e);
+    }
+    // built at the parent z keeping c's mode: z's grouped channels (or, at
+    // the root, the terms one by one) with the siblings' parts
+    void define_dg(int c, int a, int b, const Key& in, int slot) {
+        const int z = t.parent[c];
+        const int k = (int)(std::find(t.ch[z].begin(), t.ch[z].end(), c) - t.ch[z].begin());
+        std::vector<Proto> es;
+        std::set<CKey> seen;
+        for (size_t r = 0; r < h.terms.size(); ++r) {
+            if (h.bra[r] != a || h.ket[r] != b || !crossing(r, c) || restrict_to(h.terms[r], c, true) != in) continue;
+            term_at(z, r, k, slot, seen, es);
+        }
+        auto& dst = dn_env[c][{a, b}];
+        dst.insert(dst.end(), es.begin(), es.end());
     }
     int get_loc(int c, int a) {
         if (!has_loc[c][a]) return -1;
@@ -1223,7 +1293,7 @@ struct MsBuilder {
     }
     // slot list of a term part `key` (the whole term, or its part on one
     // side of a bond) on the modes of node z, skipping mode `skip`
-    std::vector<int> mode_slots(int z, int a, int b, const Key& key, int skip) {
+    std::vector<int> mode_slots(int z, int a, int b, const Key& key, int skip, bool parent = true) {
         const int D = (int)t.dims[z].size();
         std::vector<int> sl(D, -1);
         if (t.leaf(z)) {
@@ -1238,7 +1308,7 @@ struct MsBuilder {
                 sl[k] = chan(true, ck, a, b, restrict_to(key, ck, true));
             }
         }
-        if (z > 0 && skip != D - 1) sl[D - 1] = chan(false, z, a, b, restrict_to(key, z, false));
+        if (parent && z > 0 && skip != D - 1) sl[D - 1] = chan(false, z, a, b, restrict_to(key, z, false));
         return sl;
     }
     void define(const Def& q) {
@@ -1249,6 +1319,7 @@ struct MsBuilder {
         e.out = q.slot;
         if (q.up == D_LOC) { define_loc(q.c, a, q.slot); return; }
         if (q.up == D_DLOC) { define_dloc(q.c, a, q.slot); return; }
+        if (q.up == D_DG) { define_dg(q.c, a, b, part, q.slot); return; }
         if (q.up == D_UP) {
             // at node c, every mode but the parent's
             e.slot = mode_slots(q.c, a, b, part, (int)t.dims[q.c].size() - 1);
@@ -1316,13 +1387,11 @@ struct MsBuilder {
             f.slot[D - 1] = sd;
             es.push_back(f);
         }
+        std::set<CKey> seen;
         for (size_t r = 0; r < h.terms.size(); ++r) {
             if (!diag(r) || h.bra[r] != a || !restrict_to(h.terms[r], c, true).empty()) continue;
             if (touched(z, h.terms[r]).size() < 2) continue;
-            Proto f;
-            f.w = h.coeff[r]; f.out = slot;
-            f.slot = mode_slots(z, a, a, h.terms[r], k);
-            es.push_back(f);
+            term_at(z, r, k, slot, seen, es);
         }
         auto& dst = dn_env[c][{a, a}];
         dst.insert(dst.end(), es.begin(), es.end());
@@ -1419,16 +1488,21 @@ struct MsBuilder {
                 if (sdl >= 0) bond[z].push_back(one(a, a, 1.0, {-1, sdl}));
                 if (konst[a] != cplx(0.0)) bond[z].push_back(one(a, a, konst[a], {-1, -1}));
             }
+            std::set<CKey> seen_h, seen_b;
             for (int r = 0; r < R; ++r) {
                 const int a = h.bra[r], b = h.ket[r];
                 if (a == b && h.terms[r].empty()) continue;          // constants: above
                 // same-set terms on one mode of z are in the local sums
-                if (a != b || touched(z, h.terms[r]).size() >= 2)
-                    heff[z].push_back(one(a, b, h.coeff[r], mode_slots(z, a, b, h.terms[r], -1)));
-                if (z == 0) continue;
-                const Key in = restrict_to(h.terms[r], z, true), out = restrict_to(h.terms[r], z, false);
-                if (a == b && (in.empty() || out.empty())) continue;  // local: above
-                bond[z].push_back(one(a, b, h.coeff[r], {chan(true, z, a, b, in), chan(false, z, a, b, out)}));
+                if (a != b || touched(z, h.terms[r]).size() >= 2) term_at(z, r, -1, -1, seen_h, heff[z]);
+                if (z == 0 || !crossing(r, z)) continue;              // local: above
+                const Key in = restrict_to(h.terms[r], z, true);
+                if (!dg_pair[z].count({a, b})) {
+                    bond[z].push_back(one(a, b, h.coeff[r], {chan(true, z, a, b, in),
+                                                             chan(false, z, a, b, restrict_to(h.terms[r], z, false))}));
+                    continue;
+                }
+                if (!seen_b.insert(CKey{a, b, in}).second) continue;
+                bond[z].push_back(one(a, b, 1.0, {chan(true, z, a, b, in), get_dg(z, a, b, in)}));
             }
         }
         close();
@@ -1440,7 +1514,7 @@ struct MsBuilder {
             bond_rng[z] = push(bond[z]);
             int nloc = 0;
             for (int a = 0; a < S; ++a) nloc += (loc_slot[z][a] >= 0) + (dloc_slot[z][a] >= 0);
-            p.op_bond_dim[z] = (int)(up_ch[z].size() + dn_ch[z].size()) + nloc;
+            p.op_bond_dim[z] = (int)(up_ch[z].size() + dn_ch[z].size() + dg_ch[z].size()) + nloc;
             for (auto& kv : up_env[z]) up_rng[z][kv.first] = push(kv.second);
             for (auto& kv : dn_env[z]) dn_rng[z][kv.first] = push(kv.second);
         }

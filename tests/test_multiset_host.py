@@ -2,10 +2,13 @@
 ansatz), on host-resident contexts (no GPU): the channels crossing every
 bond -- counted here by brute force -- are, per set, one pre-summed local
 channel for its terms acting only inside the subtree and one for those
-acting only outside, plus one channel per distinct (bra set, ket set, part
-of a term on that side) for the same-set terms acting on both sides and
-for every term coupling two sets (whose empty parts are overlaps, not
-identities); set counts that do not match are refused."""
+acting only outside, plus, for the terms crossing the bond (same-set terms
+acting on both sides, and every term coupling two sets, whose empty parts
+are overlaps rather than identities), per set pair: one single-particle
+channel and one grouped mean-field channel per distinct inside part where
+the pair has fewer distinct inside than outside parts there, else one
+channel per distinct inside part and one per distinct outside part; set
+counts that do not match are refused."""
 import numpy as np
 import pytest
 
@@ -17,7 +20,7 @@ def expected_dims(tree, H):
     out = np.zeros(tree.n, dtype=np.int32)
     for c in range(1, tree.n):
         inside = set(tree.subtree_leaves(c))
-        ups, dns, loc, dloc = set(), set(), set(), set()
+        ins, outs, loc, dloc = {}, {}, set(), set()
         for fs, a, b, coef in zip(H.factors, H.bra, H.ket, H.coeffs):
             if coef == 0:
                 continue
@@ -29,10 +32,11 @@ def expected_dims(tree, H):
                 elif fout and not fin:
                     dloc.add(a)
                 elif fin and fout:
-                    ups.add((a, b, fin)); dns.add((a, b, fout))
+                    ins.setdefault((a, b), set()).add(fin); outs.setdefault((a, b), set()).add(fout)
             else:
-                ups.add((a, b, fin)); dns.add((a, b, fout))
-        out[c] = len(loc) + len(dloc) + len(ups) + len(dns)
+                ins.setdefault((a, b), set()).add(fin); outs.setdefault((a, b), set()).add(fout)
+        crossing = sum(2 * len(ins[k]) if len(ins[k]) < len(outs[k]) else len(ins[k]) + len(outs[k]) for k in ins)
+        out[c] = len(loc) + len(dloc) + crossing
     return out
 
 
