@@ -655,6 +655,8 @@ def run_serving(args):
     ranges = dict(SERVE_RANGES)
     if args.serve_full:
         ranges = dict(n_modes_range=(8, 128), d_range=(8, 20), chi_range=(8, 48), steps_range=(100, 400))
+    if args.serve_steps_range:
+        ranges["steps_range"] = tuple(args.serve_steps_range)
     res = serve_stream(ttn, W, args.serve_requests, ranges, args.slice_ms, burst=True,
                        sample=args.serve_sample, sample_steps=args.serve_sample_steps,
                        log=lambda m: print(f"[serve] {m}", file=sys.stderr, flush=True))
@@ -692,6 +694,8 @@ def main():
     ap.add_argument("--acc-instances", type=int, default=2)
     ap.add_argument("--acc-cluster", type=int, default=16)
     ap.add_argument("--serve-requests", type=int, default=512)
+    ap.add_argument("--serve-steps-range", type=int, nargs=2, default=None, metavar=("LO", "HI"),
+                    help="override the requests' step counts (a bounded sample of the same size ranges)")
     ap.add_argument("--serve-full", action="store_true",
                     help="--serve with the paper-shaped ranges (8-128 modes, bond dims 8-48, 100-400 steps)")
     ap.add_argument("--default-serve-requests", type=int, default=160,
