@@ -448,9 +448,14 @@ def run_reference(args, rank, world):
             "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": workload_name(1), "global_batch": 1, "precision": "fp64 (oracle)"},
+            # the same workload as our arm; each timed step is a bounded
+            # sample of it: one step of one of its instances (instance-steps/s)
+            "config": {"workload": workload_name(args.batch), "global_batch": args.batch * world,
+                       "instances_per_gpu": args.batch, "precision": "fp64 (oracle)",
+                       "sample": "each step: one TDVP step of instance 0 (seed 2) of the batch"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{args.steps} timed TDVP steps of 1 instance (seed 2), NumPy complex128"},
+                             "sample": f"{args.steps} timed TDVP steps of 1 instance (seed 2) of the "
+                                       f"{args.batch}-instance workload, NumPy complex128"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
