@@ -433,7 +433,7 @@ ttn_status ttn_mode_product_c64(void* stream, int64_t L, int n, int64_t R, const
                                 double wr, double wi, int accumulate, int tensor_cores);
 
 /* Measured arithmetic peaks of the current device (no counterpart in the
- * paper: the denominators of the roofline the sweep kernel is judged
+ * paper: the denominators of the roofline the sweep kernel is measured
  * against).  fp32_tflops / fp64_tflops receive the sustained rate of fused
  * multiply-adds (2 flops each) of a kernel that fills every SM with
  * independent FMA chains, timed with CUDA events on `stream` (NULL: the
