@@ -206,8 +206,9 @@ ttn_status ttn_set_coefficients(ttn_ctx* ctx, int n_terms, const ttn_c128* coeff
  * ttn_step (no subspace expansion: the paper leaves it open for this
  * ansatz), ttn_step_batch, the request server, ttn_norm_energy (whole
  * state), ttn_set_populations and the state calls below; the single-set
- * state, density, vacuum-projection, ground-state and checkpoint calls
- * return TTN_E_INVALID. */
+ * state, density, vacuum-projection and ground-state calls return
+ * TTN_E_INVALID.  ttn_save / ttn_load carry multi-set states too (the set
+ * count and set pairs with the operator, every set's tensors). */
 ttn_status ttn_set_multiset_hamiltonian(ttn_ctx* ctx, int n_sets, int n_terms, const ttn_c128* coeff,
                                         const int* term_ptr, const int* factor_leaf,
                                         const ttn_c128* factor_mats, const int64_t* factor_mat_off,
@@ -237,8 +238,9 @@ ttn_status ttn_n_sets(const ttn_ctx* ctx, int* n_sets);
  * are resumed from saved states).  ttn_save writes the tree (with the
  * current bond dimensions, which subspace expansion may have grown), the
  * step and flop counters, the Hamiltonian as last given (coefficients,
- * factors, matrices, hermitian flag) and every node tensor (complex128,
- * centre at the root) into buf, a self-describing byte stream of *len
+ * factors, matrices, hermitian flag; for a multi-set state also the set
+ * count and every term's set pair) and every node tensor (complex128,
+ * centre at the root; all set blocks) into buf, a self-describing byte stream of *len
  * bytes; with buf == NULL it only stores the required size in *len, and a
  * too small *len gives TTN_E_INVALID with the size in *len.  ttn_load
  * replaces the tree, state, Hamiltonian and counters of ctx by those of a

@@ -546,6 +546,9 @@ struct Reader {
     }
 };
 const uint32_t kCkptMagic = 0x314E5454u;   // "TTN1"
+// A multi-set checkpoint: after the Hamiltonian, the set count and every
+// term's set pair; each node's tensor holds all set blocks (set 0 first).
+const uint32_t kCkptMagicSets = 0x324E5454u;   // "TTN2"
 
 }  // namespace
 
@@ -795,8 +798,8 @@ ttn_status ttn_n_sets(const ttn_ctx* c, int* n_sets) {
 
 ttn_status ttn_save(ttn_ctx* c, void* buf, size_t* len) {
     ttn_status u = usable(c); if (u) return u;
-    if (c->plan.nset > 1) return fail(c, TTN_E_INVALID, "checkpoints hold single-set states");
     if (!len) return fail(c, TTN_E_INVALID, "len is NULL");
+    const bool sets = c->plan.nset > 1;
     std::vector<std::vector<cplx>> A;
     int64_t steps = c->saved_steps;
     double flops[2] = {c->saved_flops, c->saved_flops64};
@@ -812,7 +815,7 @@ ttn_status ttn_save(ttn_ctx* c, void* buf, size_t* len) {
         A = c->host_A;
     }
     Writer w;
-    w.put<uint32_t>(kCkptMagic);
+    w.put<uint32_t>(sets ? kCkptMagicSets : kCkptMagic);
     w.put<int32_t>(c->precision);
     w.put_vec(c->tree.parent);
     w.put_vec(c->tree.phys);
@@ -829,6 +832,11 @@ ttn_status ttn_save(ttn_ctx* c, void* buf, size_t* len) {
     w.put_vec(c->sop_leaf);
     w.put_vec(c->sop_off);
     w.put_vec(c->sop_mats);
+    if (sets) {
+        w.put<int32_t>(c->sop_nsets);
+        w.put_vec(c->sop_bra);
+        w.put_vec(c->sop_ket);
+    }
     for (int z = 0; z < c->tree.n; ++z) w.put_vec(A[z]);
     const size_t need = w.b.size();
     if (!buf) { *len = need; return TTN_OK; }
@@ -843,7 +851,9 @@ ttn_status ttn_load(ttn_ctx* c, const void* buf, size_t len) {
     if (!buf) return fail(c, TTN_E_INVALID, "buf is NULL");
     Reader r{(const char*)buf, len};
     const int64_t big = (int64_t)1 << 40;
-    if (r.get<uint32_t>() != kCkptMagic || !r.ok) return fail(c, TTN_E_INVALID, "not a libttn checkpoint");
+    const uint32_t magic = r.get<uint32_t>();
+    if ((magic != kCkptMagic && magic != kCkptMagicSets) || !r.ok)
+        return fail(c, TTN_E_INVALID, "not a libttn checkpoint");
     r.get<int32_t>();                                // precision of the saving context (informational)
     std::vector<int> parent = r.get_vec<int>(65535), phys = r.get_vec<int>(65535), bond = r.get_vec<int>(65535);
     const int64_t steps = r.get<int64_t>();
@@ -853,6 +863,16 @@ ttn_status ttn_load(ttn_ctx* c, const void* buf, size_t len) {
     std::vector<int> ptr = r.get_vec<int>(big), leaf = r.get_vec<int>(big);
     std::vector<int64_t> off = r.get_vec<int64_t>(big);
     std::vector<cplx> mats = r.get_vec<cplx>(big);
+    int nsets = 1;
+    std::vector<int> bra, ket;
+    if (magic == kCkptMagicSets) {
+        nsets = r.get<int32_t>();
+        bra = r.get_vec<int>(big);
+        ket = r.get_vec<int>(big);
+        if (r.ok && (nsets < 2 || nsets > TTN_MAX_SETS || !has_h || bra.size() != coeff.size() ||
+                     ket.size() != coeff.size()))
+            return fail(c, TTN_E_INVALID, "inconsistent multi-set checkpoint");
+    }
     if (!r.ok || parent.size() != phys.size() || parent.size() != bond.size() || parent.empty())
         return fail(c, TTN_E_INVALID, "truncated or inconsistent checkpoint");
     ttn::Tree t;
@@ -861,17 +881,19 @@ ttn_status ttn_load(ttn_ctx* c, const void* buf, size_t len) {
     std::vector<std::vector<cplx>> A(t.n);
     for (int z = 0; z < t.n; ++z) {
         A[z] = r.get_vec<cplx>(big);
-        if (!r.ok || (int64_t)A[z].size() != t.size[z]) return fail(c, TTN_E_INVALID, "checkpoint tensor " + std::to_string(z) + " has the wrong size");
+        if (!r.ok || (int64_t)A[z].size() != nsets * t.size[z])
+            return fail(c, TTN_E_INVALID, "checkpoint tensor " + std::to_string(z) + " has the wrong size");
     }
+    ttn::Hamiltonian h;
+    ttn::Plan probe;                                 // plan now, so nothing fails after ctx is modified
     if (has_h) {
         const int nt = (int)coeff.size();
         if ((int)ptr.size() != nt + 1 || ptr[nt] != (int)leaf.size() || leaf.size() != off.size())
             return fail(c, TTN_E_INVALID, "inconsistent Hamiltonian in the checkpoint");
-        ttn::Hamiltonian h;
         msg = ttn::build_hamiltonian(t, nt, coeff.data(), ptr.data(), leaf.empty() ? nullptr : leaf.data(),
-                                     mats.empty() ? nullptr : mats.data(), off.empty() ? nullptr : off.data(), herm, h);
+                                     mats.empty() ? nullptr : mats.data(), off.empty() ? nullptr : off.data(), herm, h,
+                                     nsets, bra.empty() ? nullptr : bra.data(), ket.empty() ? nullptr : ket.data());
         if (!msg.empty()) return fail(c, TTN_E_INVALID, "checkpoint Hamiltonian: " + msg);
-        ttn::Plan probe;                             // plan now, so nothing fails after ctx is modified
         msg = ttn::make_plan(t, &h, c->precision, probe);
         if (!msg.empty()) return fail(c, TTN_E_INVALID, "checkpoint Hamiltonian: " + msg);
     }
@@ -897,7 +919,16 @@ ttn_status ttn_load(ttn_ctx* c, const void* buf, size_t len) {
     c->saved_flops64 = f1;
     c->sop_coeff.clear(); c->sop_ptr.clear(); c->sop_leaf.clear(); c->sop_off.clear(); c->sop_mats.clear();
     c->sop_nsets = 1; c->sop_bra.clear(); c->sop_ket.clear();
-    if (has_h) {
+    if (nsets > 1) {
+        // the set blocks are restored as saved: the multi-set plan and
+        // operator directly, no conversion of a single-set state
+        c->plan = probe;
+        c->ham = h;
+        c->has_h = true;
+        c->sop_coeff = coeff; c->sop_ptr = ptr; c->sop_leaf = leaf; c->sop_off = off; c->sop_mats = mats;
+        c->sop_herm = herm;
+        c->sop_nsets = nsets; c->sop_bra = bra; c->sop_ket = ket;
+    } else if (has_h) {
         ttn_status s = ttn_set_sop_hamiltonian(c, (int)coeff.size(), (const ttn_c128*)coeff.data(), ptr.data(),
                                                leaf.empty() ? nullptr : leaf.data(),
                                                mats.empty() ? nullptr : (const ttn_c128*)mats.data(),

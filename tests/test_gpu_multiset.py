@@ -180,7 +180,7 @@ def test_multiset_refuses_single_set_calls(gpu_lib):
     p = W.multiset_vibronic_problem(n_states=2, n_modes=4, d=5, chi=3)
     c = ctx_for(gpu_lib, p.tree, p.H, p.tensors, gpu_lib.TTN_FP64)
     leaf = p.meta["modes"][0]
-    for call in (lambda: c.rdm(leaf), lambda: c.ground_state(1), lambda: c.save(),
+    for call in (lambda: c.rdm(leaf), lambda: c.ground_state(1),
                  lambda: c.set_state(p.tensors[0]), lambda: c.vacuum_projection(leaf),
                  lambda: c.step(p.dt, 1, {"expand": 1, "eps_spawn": 1e-6, "chi_max": 8})):
         with pytest.raises(gpu_lib.TTNError):
@@ -237,3 +237,22 @@ def test_multiset_requests_through_the_server(gpu_lib):
     srv.close()
     for c in alone + served:
         c.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_multiset_checkpoint_resume_is_bit_identical(gpu_lib, precision):
+    """Save a resident multi-set context mid-run, load it into a fresh
+    context, and both continue with the same bits."""
+    p = W.multiset_vibronic_problem(n_states=3, n_modes=5, d=5, chi=3, amps=OCCUPIED)
+    a = ctx_for(gpu_lib, p.tree, p.H, p.tensors, precision)
+    a.step(p.dt, 4)
+    blob = a.save()
+    other = W.config_c1()
+    b = gpu_lib.Context(other.tree, precision)
+    b.load(blob)
+    assert b.n_sets() == 3
+    a.step(p.dt, 4)
+    b.step(p.dt, 4)
+    np.testing.assert_array_equal(gpu_full(a, p.tree, 3), gpu_full(b, p.tree, 3))
+    a.close()
+    b.close()

@@ -88,3 +88,32 @@ def test_bad_set_index_is_refused():
     with pytest.raises(ttn.TTNError):
         c.set_multiset_hamiltonian(H)
     c.close()
+
+
+def test_multiset_checkpoint_round_trip_on_the_host():
+    """A multi-set checkpoint restores the set count, the operator (channel
+    counts), every set's tensors bit for bit and the coefficients' replay;
+    a truncated one is refused and leaves the target context unchanged."""
+    from paper_2503_15460_gb300 import ttn
+    rng = np.random.default_rng(9)
+    t = small_tree(False)
+    H = coupled_sop(t, rng)
+    A = W.multiset_product_state(t, [0.6, 0.48j, 0.64])
+    c = host_ctx(t, H)
+    c.set_multiset_state(A)
+    blob = c.save()
+    d = ttn.Context(W.build_tree(("node", 1, [("leaf", 2, 2, "a"), ("leaf", 3, 3, "b")])), ttn.TTN_FP64, on_host=True)
+    with pytest.raises(ttn.TTNError):
+        d.load(blob[: len(blob) // 2])
+    assert d.n_sets() == 1
+    d.load(blob)
+    assert d.n_sets() == 3
+    np.testing.assert_array_equal(d.operator_dims(), c.operator_dims())
+    for a in range(3):
+        for x, y in zip(c.get_multiset_state(a), d.get_multiset_state(a)):
+            np.testing.assert_array_equal(x, y)
+    d.set_coefficients(np.asarray(H.coeffs) * 0.5)      # the stored set pairs are replayed
+    assert d.n_sets() == 3
+    np.testing.assert_array_equal(d.operator_dims(), c.operator_dims())
+    c.close()
+    d.close()
