@@ -79,3 +79,48 @@ def test_thermal_spectral_density_zero_temperature_limit():
     # a large but finite beta approaches it
     np.testing.assert_allclose(W.thermal_J(J, 200.0)(w[np.abs(w) > 0.5]),
                                np.where(w[np.abs(w) > 0.5] > 0, J(w[np.abs(w) > 0.5]), 0.0), atol=1e-30)
+
+
+def test_multiset_vibronic_generator_is_the_model_formula():
+    """The shared multi-set vibronic generator against its formula written
+    with Kronecker products (set index slowest, leaves in node order):
+    sum_s |s><s| (x) [E_s + sum_i w_i (n_i + 1/2) + sum_i kappa_i^s Q_i]
+    + sum_{s != s'} |s><s'| (x) [J_{ss'} + sum_j lam_j^{ss'} Q_{c_j}],
+    J and lam symmetric in (s, s'), Q = (a + a^+)/sqrt 2."""
+    from oracle import exact
+    p = W.multiset_vibronic_problem(n_states=3, n_modes=3, d=3, chi=3, seed=4)
+    m = p.meta
+    S, d = 3, m["d"]
+    leaves = p.tree.leaves()
+    pos = {int(l): k for k, l in enumerate(leaves)}           # leaf -> Kronecker position
+    mode_pos = [pos[int(l)] for l in m["modes"]]
+    a = np.diag(np.sqrt(np.arange(1, d)), 1)
+    Q = (a + a.T) / np.sqrt(2.0)
+    num = np.diag(np.arange(d) + 0.5)
+    I = np.eye(d)
+
+    def on(k, M):                                              # M on Kronecker position k
+        out = np.ones((1, 1))
+        for j in range(len(leaves)):
+            out = np.kron(out, M if j == k else I)
+        return out
+
+    D = d ** len(leaves)
+    want = np.zeros((S * D, S * D), dtype=np.complex128)
+    for s in range(S):
+        blk = m["E"][s] * np.eye(D)
+        for i in range(3):
+            blk = blk + m["omega"][i] * on(mode_pos[i], num) + m["kappa"][i, s] * on(mode_pos[i], Q)
+        want[s * D:(s + 1) * D, s * D:(s + 1) * D] += blk
+    for s in range(S):
+        for s2 in range(S):
+            if s == s2:
+                continue
+            lo, hi = min(s, s2), max(s, s2)
+            blk = m["J"][lo, hi] * np.eye(D)
+            for j, i in enumerate(m["coupling_modes"]):
+                blk = blk + m["lam"][j, lo, hi] * on(mode_pos[i], Q)
+            want[s * D:(s + 1) * D, s2 * D:(s2 + 1) * D] += blk
+    got = exact.full_multiset_hamiltonian(p.tree, p.H, dense=True)
+    assert np.abs(got - want).max() <= 1e-14
+    assert np.abs(got - got.conj().T).max() <= 1e-15

@@ -692,7 +692,8 @@ def multiset_vibronic_problem(n_states: int = 3, n_modes: int = 6, d: int = 6, c
     amps = np.asarray(amps, dtype=np.complex128)
     A = multiset_product_state(t, list(amps / np.linalg.norm(amps)))
     return MultiSetProblem(f"multiset_vibronic_{n_states}x{n_modes}_d{d}_chi{chi}_seed{seed}", t, H, A,
-                           dt, nsteps, {"modes": modes, "coupling_modes": cm})
+                           dt, nsteps, {"modes": modes, "coupling_modes": cm, "omega": omega, "E": E,
+                                        "kappa": kappa, "J": J, "lam": lam, "d": d})
 
 
 def c5_problem(req: dict) -> Problem:
